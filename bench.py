@@ -1,0 +1,377 @@
+"""Benchmark of the sigma_min grid engine on one GB300 (or N replicas).
+
+One step = one full-grid evaluation of sigma_min(zI - A) and its eight
+epsilon masks for the mid-size workload: a random non-normal banded Toeplitz
+matrix (n = 2000, kl = 2, ku = 5, complex coefficients Re, Im ~ N(0,1), seed 0,
+superdiagonals scaled by 4) on a 512 x 512 grid over the bounding box of its
+symbol curve widened by 20 %, eps = 1e-1 ... 1e-8, Lanczos to convergence
+(tol 1e-13). Inputs are synthetic and seeded.
+
+Printed JSON line (rank 0): points/s of the whole job, the roofline of the
+dominant kernel (FP64-ALU bound; algorithmic flops / CUDA-event time), the
+end-to-end rate through the public API with host buffers, the CPU oracle on a
+bounded sample, the restricted-versus-full-grid time on the 5 x 5-dilated
+sensitive zone (paper Sec. 4), and the SM clocks seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 it runs under torch.distributed.run, one process per GPU;
+each rank evaluates the full workload on its own GPU (replicas: the method has
+no exchange step) and the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2605_04550_gb300 import inputs  # noqa: E402
+
+METRIC = "σ_min grid points/s (FP64); restricted vs full-grid time at ≥99% sensitive recall"
+UNIT = "grid points/s"
+N, KL, KU, SEED, NX, NY = 2000, 2, 5, 0, 512, 512
+EPS = inputs.EPS_LEVELS_8
+EPS_RESTRICT = 1e-2
+TOL, KMAX = 1e-13, 1000
+WORKLOAD = (f"random banded Toeplitz n={N} kl={KL} ku={KU} (complex N(0,1) coefficients, seed {SEED}, "
+            f"superdiagonals x4), {NX}x{NY} grid over the symbol-curve bounding box +20%, "
+            f"8 eps levels 1e-1..1e-8, Lanczos to convergence (tol {TOL:g})")
+# nominal FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+# reduced case for profiler captures: same matrix family, n = 256, one wave of
+# 38,896 points (208 x 187 grid), k_max 300 -> about 2.3 GB of workspace
+SMALL = dict(n=256, nx=208, ny=187, kmax=300)
+
+
+def workload(case: str = "mid"):
+    n, nx, ny = (N, NX, NY) if case == "mid" else (SMALL["n"], SMALL["nx"], SMALL["ny"])
+    bands, kl, ku, a = inputs.random_toeplitz(n, KL, KU, seed=SEED)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, nx, ny)
+    return bands, kl, ku, grid
+
+
+def algorithmic_flops(steps: np.ndarray, n: int, kl: int, ku: int) -> float:
+    """n (8 kl (kl+ku) + 6 kl + 8) per banded LU + n (16 (2kl+ku) + 30) per Lanczos step."""
+    steps = np.asarray(steps, dtype=np.float64)
+    lu = n * (8 * kl * (kl + ku) + 6 * kl + 8)
+    per_step = n * (16 * (2 * kl + ku) + 30)
+    return float(steps.size * lu + steps.sum() * per_step)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(bands, kl, ku, grid, seconds: float = 12.0, seed: int = 1):
+    """The CPU oracle (as it stands, OpenMP over points, all host cores) on random
+    points of the same grid with the library's stopping settings, until `seconds`."""
+    import oracle
+    z = oracle.grid_points(grid).ravel()
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(z.size)
+    done, t0, batch = 0, time.perf_counter(), 256
+    while True:
+        sel = order[done:done + batch]
+        oracle.sigma_min_banded(bands, kl, ku, z[sel], k_min=2, k_max=KMAX, tol=TOL)
+        done += sel.size
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= z.size:
+            break
+        batch = min(4096, batch * 2)
+    cores = os.cpu_count() or 1
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} uniformly random points of the {NX}x{NY} grid (same matrix, tol {TOL:g}, "
+                      f"k_max {KMAX}), {el:.1f} s on {cores} host threads (OpenMP)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    bands, kl, ku, grid = workload()
+    import oracle
+    oracle.build()
+    z = oracle.grid_points(grid).ravel()
+    rng = np.random.default_rng(7)
+    per_step = 512
+    order = rng.permutation(z.size)
+    for w in range(args.warmup):
+        oracle.sigma_min_banded(bands, kl, ku, z[order[:64]], k_min=2, k_max=KMAX, tol=TOL)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        sel = order[(s * per_step) % z.size:][:per_step]
+        oracle.sigma_min_banded(bands, kl, ku, z[sel], k_min=2, k_max=KMAX, tol=TOL)
+    el = time.perf_counter() - t0
+    value = args.steps * per_step / el
+    cores = os.cpu_count() or 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_step": per_step,
+                   "note": "CPU oracle (banded LU + inverse Lanczos in C, OpenMP); each step a random "
+                           f"{per_step}-point sample of the grid"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} x {per_step} random grid points"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def dilate(mask2d: np.ndarray, k: int) -> np.ndarray:
+    """Binary dilation with a k x k square (paper Sec. 3.6 / Sec. 4: 5 x 5 for R, 3 x 3 for truth)."""
+    r = k // 2
+    m = np.pad(mask2d, r)
+    out = np.zeros_like(mask2d)
+    for di in range(k):
+        for dj in range(k):
+            out |= m[di:di + mask2d.shape[0], dj:dj + mask2d.shape[1]]
+    return out
+
+
+def run_gpu(args):
+    import torch
+    import paper_2605_04550_gb300 as psa
+
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bands, kl, ku, grid = workload(args.case)
+    n = bands.shape[1]
+    npts = grid.npoints
+    b_dev = torch.as_tensor(bands, device=dev)
+    opts = psa.LanczosOpts(k_min=2, k_max=KMAX if args.case == "mid" else SMALL["kmax"], tol=TOL, seed=0)
+    pif = psa.default_points_in_flight(npts)
+    wsp = psa.Workspace(n, kl, ku, pif, opts, device=dev)
+    out = psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        if ws_ > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp, out=out)
+    torch.cuda.synchronize(dev)
+
+    # ---------------- timed region: K full-grid steps, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp, out=out)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = float(np.sum(step_ms))
+    if ws_ > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    value = ws_ * npts * args.steps / (dev_ms * 1e-3)
+
+    steps = out.steps.cpu().numpy().ravel()
+    status = out.status.cpu().numpy().ravel()
+    sig = out.sigma.cpu().numpy()
+    mask = out.mask.cpu().numpy().view(np.uint32)
+    flops = algorithmic_flops(steps, n, kl, ku)
+    mean_ms = dev_ms / args.steps if ws_ == 1 else float(np.mean(step_ms))
+    achieved = flops / (mean_ms * 1e-3) / 1e12
+    # lanes idle inside a warp: steps of 32 consecutive points vs the warp's maximum
+    sw = steps[: steps.size // 32 * 32].reshape(-1, 32)
+    lane_util = float(sw.sum() / (sw.max(axis=1).sum() * 32))
+
+    if args.case != "mid":
+        if rank == 0:
+            print(json.dumps({"case": args.case, "n": n, "points": npts, "ms_per_step": mean_ms,
+                              "points_per_s": npts / (mean_ms * 1e-3), "achieved_tflops": achieved,
+                              "mean_lanczos_steps": float(steps.mean()), "lane_utilisation": lane_util}),
+                  flush=True)
+        return 0
+
+    # ---------------- end to end through the public API with host buffers
+    pinned_b = torch.as_tensor(bands).pin_memory()
+    h_sigma = torch.empty((grid.ny, grid.nx), dtype=torch.float64).pin_memory()
+    h_mask = torch.empty((grid.ny, grid.nx), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bd = pinned_b.to(dev, non_blocking=True)
+        o2 = psa.sigma_min(bd, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp)
+        h_sigma.copy_(o2.sigma, non_blocking=True)
+        h_mask.copy_(o2.mask, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": npts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(bands.nbytes),
+           "d2h_bytes_per_step": int(h_sigma.numel() * 8 + h_mask.numel() * 4)}
+
+    # ---------------- restricted (paper Sec. 4) vs full grid, region = 5x5-dilated S_eps
+    lvl = EPS.index(EPS_RESTRICT)
+    s_true = ((mask >> lvl) & 1).astype(bool)
+    region = dilate(s_true, 5)
+    idx = torch.as_tensor(np.flatnonzero(region.ravel()).astype(np.int32), device=dev)
+    psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, idx=idx, opts=opts, workspace=wsp)
+    torch.cuda.synchronize(dev)
+    r_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    flush.fill_(-1.0)
+    r_ev[0].record(stream)
+    out_r = psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, idx=idx, opts=opts, workspace=wsp)
+    r_ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    r_ms = r_ev[0].elapsed_time(r_ev[1])
+    mask_r = out_r.mask.cpu().numpy().view(np.uint32)
+    s_pred = ((mask_r >> lvl) & 1).astype(bool)
+    truth_d = dilate(s_true, 3)
+    recall = float((truth_d & region).sum() / max(truth_d.sum(), 1))
+    coverage = float((s_true & s_pred).sum() / max(s_true.sum(), 1))
+    same = bool(np.array_equal(out_r.sigma.cpu().numpy()[region], sig[region]))
+    restricted = {"eps": EPS_RESTRICT, "region": "5x5 dilation of the full-grid sensitive zone",
+                  "grid_fraction": float(region.mean()), "recall_dilated_truth": recall,
+                  "coverage": coverage, "full_ms": mean_ms, "restricted_ms": r_ms,
+                  "speedup": mean_ms / r_ms if r_ms > 0 else None, "sigma_bitwise_equal_on_region": same}
+
+    probe = psa.probe_dfma_rate(4096)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_step": npts, "points_in_flight": pif,
+                   "workspace_gb": wsp.nbytes / 1e9,
+                   "l2": "L2 flushed (256 MB write) between timed steps; per-step workspace (factors, "
+                         "Lanczos vectors) of tens of GB also exceeds L2",
+                   "parallelism": "replicas" if ws_ > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "peak_probe_tflops": 2 * probe / 1e12,
+                     "frac_of_probe": achieved / (2 * probe / 1e12),
+                     "algorithmic_flops_per_launch": flops,
+                     "kernel": "k_sigma_min<2,5> (+ three set-up kernels of a few microseconds)"},
+        "cpu_baseline": None,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "mean_lanczos_steps": float(steps.mean()),
+        "max_lanczos_steps": int(steps.max()),
+        "lane_utilisation": lane_util,
+        "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
+        "restricted": restricted,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(bands, kl, ku, grid, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--case", default="mid", choices=["mid", "small"],
+                    help="mid: the benchmark workload; small: reduced case for profiler captures")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

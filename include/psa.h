@@ -1,0 +1,165 @@
+/*
+ * psa.h -- C ABI of the GB300 sigma_min grid engine (libpsa.so).
+ *
+ * The library evaluates sigma_min(zI - A), the smallest singular value of
+ * zI - A, at the points z of a rectangular complex grid or of a list of grid
+ * points, for a banded complex matrix A, and thresholds it at a list of
+ * epsilon levels. This is the quantity whose level sets are the
+ * epsilon-pseudospectra (paper Sec. 2, Definition "Pseudospectrum": the set
+ * {z : sigma_min(zI - A) <= eps}), evaluated on the grid of Sec. 2.1 and, in
+ * restricted mode, only on the predicted region R of the hybrid method
+ * (Sec. 4: sigma_min is computed exactly for z in R and every other point is
+ * classified non-sensitive).
+ *
+ * Method per point (hand-written CUDA for sm_103a, complex FP64 throughout):
+ * B = zI - A is factored by banded Gaussian elimination with partial pivoting
+ * (pivot = largest |Re| + |Im| in the column, first on ties; U gains kl
+ * extra superdiagonals), then the Lanczos process on H = (B B^*)^{-1}, each
+ * product formed by four banded triangular sweeps, gives
+ * sigma_min = lambda_max(H)^{-1/2}. The paper computes the same quantity with a
+ * dense SVD (Sec. 2.1); the banded path gives it in O(n (2kl+ku)) work per
+ * Lanczos step instead of O(n^3).
+ *
+ * Conventions shared by every call:
+ *  - All calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream); the library never synchronises the device and
+ *    allocates no memory. The caller owns every buffer.
+ *  - Device pointers must point to memory of the current CUDA device.
+ *  - Return value: PSA_OK (0) or a negative PSA_E* code; psa_strerror()
+ *    gives its text. On error nothing is launched.
+ */
+#ifndef PSA_H
+#define PSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define PSA_OK 0
+#define PSA_EINVAL (-1)      /* an argument is out of range or a required pointer is NULL */
+#define PSA_EWORKSPACE (-2)  /* workspace too small (or NULL) for even one warp of points */
+#define PSA_ECUDA (-3)       /* a CUDA launch or query failed (see cudaGetLastError) */
+#define PSA_EUNSUPPORTED (-4) /* band widths beyond kl <= 4, ku <= 8 */
+
+/* ----------------------------------------------------- per-point status */
+#define PSA_PT_OK 0             /* converged (or fixed step count completed) */
+#define PSA_PT_SINGULAR 1       /* exact zero pivot column: B singular, sigma = 0 */
+#define PSA_PT_NOT_CONVERGED 2  /* k_max steps without meeting the stopping test */
+#define PSA_PT_NONFINITE 3      /* A has a non-finite entry in its band: sigma = 0 */
+#define PSA_PT_NOT_EVALUATED 4  /* restricted mode: point not in the list; sigma = NaN,
+                                   mask = 0 (non-sensitive, paper Sec. 4) */
+#define PSA_PT_UNDERFLOW 5      /* sigma_min below the double range (a solve overflowed,
+                                   |(zI - A)^{-1}| > ~1e308): sigma reported as 0 */
+
+/* Complex FP64, layout-identical to cuDoubleComplex and torch.complex128. */
+typedef struct {
+    double re, im;
+} psa_c64;
+
+/* Band matrix A of order n with kl subdiagonals and ku superdiagonals.
+ * `bands` is a DEVICE pointer to (kl + ku + 1) * n values, diagonal-major:
+ *   bands[(d + kl) * n + i] = A[i][i + d],  d in [-kl, ku], i in [0, n).
+ * Entries with i + d outside [0, n) are never read. Read-only. */
+typedef struct {
+    int32_t n, kl, ku;
+    const psa_c64 *bands;
+} psa_band;
+
+/* Grid of the complex plane (paper Sec. 2.1): nx abscissae and ny ordinates,
+ *   x_j = fma(j, (re_max - re_min) / (nx - 1), re_min),  j in [0, nx)
+ *   y_i = fma(i, (im_max - im_min) / (ny - 1), im_min),  i in [0, ny)
+ * (a count of 1 gives the single value re_min / im_min). Point (i, j) is
+ * z = x_j + i y_i, stored row-major at flat index i * nx + j (row = Im). */
+typedef struct {
+    double re_min, re_max, im_min, im_max;
+    int32_t nx, ny;
+} psa_grid;
+
+/* Lanczos controls.
+ *  k_min, k_max: minimum and maximum number of Lanczos steps, 1 <= k_max <= 65535,
+ *                0 <= k_min <= k_max. k_min = k_max = k runs exactly k steps
+ *                (unless the Krylov space is exhausted, beta = 0).
+ *  tol:          stopping test after step j >= max(k_min, 2): stop when the top
+ *                Ritz value moved by at most tol * theta_j,
+ *                theta_j - theta_{j-1} <= tol * theta_j.  tol >= 0.
+ *  seed:         start vector q_1 = h / |h|, h_i = u(2i) + i u(2i+1), u(c) the
+ *                c-th SplitMix64 output for this seed mapped to [-1, 1).
+ * psa_default_opts() gives k_min = 2, k_max = 1000, tol = 1e-13, seed = 0. */
+typedef struct {
+    int32_t k_min, k_max;
+    double tol;
+    uint64_t seed;
+} psa_lanczos_opts;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int psa_version(void);
+
+/* Text of a PSA_* error code (static storage). */
+const char *psa_strerror(int code);
+
+/* Default Lanczos controls (converged mode). */
+psa_lanczos_opts psa_default_opts(void);
+
+/* Bytes of device workspace that psa_sigma_min needs to keep
+ * `points_in_flight` points in flight at once (rounded up to a multiple of
+ * 32). The workspace holds, per point in flight, the pivoted band factor
+ * (n * (2kl + ku + 1) complex values and n pivot offsets), three Lanczos
+ * vectors and the tridiagonal coefficients (2 * k_max values), plus the
+ * shared start vector. Host call, no device work.
+ * Errors: PSA_EINVAL for bad A fields (bands pointer may be NULL here),
+ * bad opts, points_in_flight < 1 or bytes == NULL. */
+int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts,
+                        int64_t points_in_flight, size_t *bytes);
+
+/* Points in flight that fill the current device (SM count x 8 warps x 32),
+ * capped at `npoints` rounded up to 32. Host call (queries the device).
+ * Errors: PSA_EINVAL (npoints < 1 or out == NULL), PSA_ECUDA. */
+int psa_default_points_in_flight(int64_t npoints, int64_t *out);
+
+/* sigma_min(zI - A) and its epsilon masks over a grid.
+ *
+ *  A        band matrix (device bands), 1 <= n, 0 <= kl, ku <= n - 1,
+ *           kl <= 4, ku <= 8 (else PSA_EUNSUPPORTED).
+ *  g        grid; finite bounds with re_min <= re_max, im_min <= im_max;
+ *           nx, ny >= 1 and nx * ny <= 2^31 - 1.
+ *  eps      HOST array of n_eps levels, 0 <= n_eps <= 32, each finite and > 0.
+ *           Bit l of mask[p] is set iff sigma[p] <= eps[l] (inclusive, the
+ *           sensitive zone of paper Sec. 2.1).
+ *  idx      DEVICE array of n_idx flat grid indices (restricted mode, paper
+ *           Sec. 4) or NULL for the full grid. Entries outside [0, nx*ny) are
+ *           skipped. Points not listed get status PSA_PT_NOT_EVALUATED,
+ *           sigma = NaN, mask = 0. A listed point gets bit-for-bit the value
+ *           the full-grid call gives it (same per-point arithmetic).
+ *  sigma    DEVICE output, nx * ny doubles (required).
+ *  mask     DEVICE output, nx * ny uint32 (may be NULL).
+ *  status   DEVICE output, nx * ny int8 PSA_PT_* codes (may be NULL).
+ *  steps    DEVICE output, nx * ny int32 Lanczos steps taken (may be NULL).
+ *  opts     Lanczos controls (NULL = psa_default_opts()).
+ *  workspace, ws_bytes
+ *           DEVICE scratch of ws_bytes bytes, 256-byte aligned; its size sets
+ *           the number of points in flight (see psa_workspace_bytes); it must
+ *           not be used by another call that may run at the same time.
+ *  stream   cudaStream_t to launch on.
+ * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_EUNSUPPORTED, PSA_ECUDA. */
+int psa_sigma_min(const psa_band *A, const psa_grid *g,
+                  const double *eps, int32_t n_eps,
+                  const int32_t *idx, int64_t n_idx,
+                  double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
+                  const psa_lanczos_opts *opts,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/* Measured FP64 throughput of this device: runs a kernel of independent DFMA
+ * chains (iters iterations, 8 chains, SM count x 16 warps) on `stream`,
+ * synchronises it and returns the rate in DFMA lane-operations per second in
+ * *dfma_per_s. Used for the roofline of the FP64-bound path.
+ * Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_probe_dfma_rate(int32_t iters, double *dfma_per_s, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSA_H */

@@ -36,7 +36,7 @@ _lock = threading.Lock()
 _lib = None
 
 # status codes of the oracle (same meaning as the library's per-point codes)
-OK, SINGULAR, NOT_CONVERGED, NONFINITE = 0, 1, 2, 3
+OK, SINGULAR, NOT_CONVERGED, NONFINITE, UNDERFLOW = 0, 1, 2, 3, 5
 
 #: converged-mode settings of the exact tier
 EXACT_TOL = 1e-15

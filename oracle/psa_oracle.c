@@ -40,7 +40,10 @@
  *      (status NOT_CONVERGED). sigma = 2^(-e1) / sqrt(theta_j).
  *
  * Per-point status: 0 OK, 1 SINGULAR (an exact zero pivot column: sigma = 0),
- * 2 NOT_CONVERGED (k_max reached), 3 NONFINITE (a non-finite value appeared).
+ * 2 NOT_CONVERGED (k_max reached), 3 NONFINITE (a band entry of A is not
+ * finite: sigma = 0), 5 UNDERFLOW (a value overflowed the double range during
+ * the solves although A and z are finite, i.e. |(zI - A)^{-1}| > ~1e308 and
+ * sigma_min is below the double range: sigma = 0).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared.
  */
@@ -55,7 +58,7 @@
 
 typedef double complex cplx;
 
-enum { OR_OK = 0, OR_SINGULAR = 1, OR_NOT_CONVERGED = 2, OR_NONFINITE = 3 };
+enum { OR_OK = 0, OR_SINGULAR = 1, OR_NOT_CONVERGED = 2, OR_NONFINITE = 3, OR_UNDERFLOW = 5 };
 
 static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
@@ -63,12 +66,19 @@ static int imax(int a, int b) { return a > b ? a : b; }
 /* |Re a| + |Im a|: the pivot size used by the elimination. */
 static double cabs1(cplx a) { return fabs(creal(a)) + fabs(cimag(a)); }
 
-/* Euclidean norm of a complex vector. */
+/* Euclidean norm of a complex vector, scaled by its largest component so that
+ * the squares neither overflow nor underflow (|v| up to the largest double). */
 static double norm2_plain(int n, const cplx *v)
 {
+    double m = 0.0;
+    for (int i = 0; i < n; i++) m = fmax(m, fmax(fabs(creal(v[i])), fabs(cimag(v[i]))));
+    if (m == 0.0 || !isfinite(m)) return m;
     double s = 0.0;
-    for (int i = 0; i < n; i++) s += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
-    return sqrt(s);
+    for (int i = 0; i < n; i++) {
+        double re = creal(v[i]) / m, im = cimag(v[i]) / m;
+        s += re * re + im * im;
+    }
+    return m * sqrt(s);
 }
 
 /* ------------------------------------------------------------------ grid */
@@ -314,8 +324,14 @@ static void work_free(point_work *W)
 static int sigma_point(point_work *W, const cplx *bands, cplx z, const double *q1,
                        int k_min, int k_max, double tol, double *sigma, int *steps)
 {
-    const int n = W->F.n;
+    const int n = W->F.n, kl = W->F.kl, ku = W->F.ku;
     *steps = 0;
+    for (int d = -kl; d <= ku; d++)
+        for (int i = 0; i < n; i++)
+            if (i + d >= 0 && i + d < n && !isfinite(cabs(bands[(size_t)(d + kl) * n + i]))) {
+                *sigma = 0.0;
+                return OR_NONFINITE;
+            }
     lu_load(&W->F, bands, z);
     if (lu_factor(&W->F) != 0) { *sigma = 0.0; return OR_SINGULAR; }
 
@@ -326,7 +342,7 @@ static int sigma_point(point_work *W, const cplx *bands, cplx z, const double *q
         memcpy(W->x, W->q, sizeof(cplx) * (size_t)n);
         solve_B(&W->F, W->x);                       /* x = B^{-1} q   */
         double s = norm2_plain(n, W->x);
-        if (!isfinite(s) || s == 0.0) { *steps = j; *sigma = 0.0; return OR_NONFINITE; }
+        if (!isfinite(s) || s == 0.0) { *steps = j; *sigma = 0.0; return OR_UNDERFLOW; }
         if (j == 1) (void)frexp(s, &e1);
         for (int i = 0; i < n; i++) W->x[i] /= s;
         solve_BH(&W->F, W->x);                      /* y = B^{-*} x/|x| ; H q = s y */
@@ -342,7 +358,7 @@ static int sigma_point(point_work *W, const cplx *bands, cplx z, const double *q
         theta_prev = theta;
         oracle_tridiag_top(j, W->alpha, W->beta, &theta, &s_last);
         *steps = j;
-        if (!isfinite(theta) || !isfinite(beta) || !(theta > 0.0)) { *sigma = 0.0; return OR_NONFINITE; }
+        if (!isfinite(theta) || !isfinite(beta) || !(theta > 0.0)) { *sigma = 0.0; return OR_UNDERFLOW; }
         int done = 0;
         if (j >= k_min) {
             if (beta == 0.0) done = 1;

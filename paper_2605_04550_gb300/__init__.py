@@ -1,0 +1,167 @@
+"""GB300-native sigma_min(zI - A) grid engine for banded non-normal matrices.
+
+Python binding of libpsa (include/psa.h): argument marshalling only. Every
+step of the computation runs in the library's CUDA kernels; PyTorch provides
+device memory and streams. There is no CPU fallback: calling into the
+library without a built libpsa.so or without a CUDA device raises.
+
+    import torch, paper_2605_04550_gb300 as psa
+    from paper_2605_04550_gb300.inputs import grcar, grcar_grid_100, EPS_LEVELS_8
+    bands, kl, ku = grcar(100)
+    out = psa.sigma_min(torch.as_tensor(bands, device="cuda"), kl, ku,
+                        grcar_grid_100(), eps=EPS_LEVELS_8)
+    out.sigma   # (ny, nx) float64: sigma_min(zI - A) on the grid (paper Sec. 2.1)
+    out.mask    # (ny, nx) int32 bit l <=> sigma <= eps[l]  (Eq. (sensitive_zone))
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional, Sequence
+
+from . import _native
+from ._native import (PT_NONFINITE, PT_NOT_CONVERGED, PT_NOT_EVALUATED, PT_OK, PT_SINGULAR,
+                      PT_UNDERFLOW, PsaError)
+from .inputs import Grid
+
+__all__ = [
+    "Grid", "LanczosOpts", "SigmaMinResult", "Workspace", "sigma_min", "workspace_bytes",
+    "default_points_in_flight", "probe_dfma_rate", "library_path", "PsaError",
+    "PT_OK", "PT_SINGULAR", "PT_NOT_CONVERGED", "PT_NONFINITE", "PT_NOT_EVALUATED", "PT_UNDERFLOW",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class LanczosOpts:
+    """Lanczos controls (psa_lanczos_opts). Defaults = converged mode."""
+
+    k_min: int = 2
+    k_max: int = 1000
+    tol: float = 1e-13
+    seed: int = 0
+
+    @staticmethod
+    def fixed(k: int, seed: int = 0) -> "LanczosOpts":
+        """Exactly k Lanczos steps (k_min = k_max = k)."""
+        return LanczosOpts(k_min=k, k_max=k, tol=0.0, seed=seed)
+
+    def _c(self) -> _native.PsaLanczosOpts:
+        return _native.PsaLanczosOpts(int(self.k_min), int(self.k_max), float(self.tol),
+                                      int(self.seed) & (2**64 - 1))
+
+
+@dataclasses.dataclass
+class SigmaMinResult:
+    sigma: "object"   # torch.float64 (ny, nx)
+    mask: "object"    # torch.int32 (ny, nx) (bits; reinterpret as uint32)
+    status: "object"  # torch.int8 (ny, nx)
+    steps: "object"   # torch.int32 (ny, nx)
+
+
+def library_path() -> str:
+    return _native.LIB
+
+
+def _band(bands, kl: int, ku: int) -> _native.PsaBand:
+    import torch
+    if not isinstance(bands, torch.Tensor) or bands.dtype != torch.complex128 or not bands.is_cuda:
+        raise TypeError("bands must be a CUDA torch.complex128 tensor of shape (kl + ku + 1, n)")
+    if bands.dim() != 2 or bands.shape[0] != kl + ku + 1 or not bands.is_contiguous():
+        raise ValueError("bands must be contiguous with shape (kl + ku + 1, n)")
+    return _native.PsaBand(int(bands.shape[1]), int(kl), int(ku), bands.data_ptr())
+
+
+def _band_shape(n: int, kl: int, ku: int) -> _native.PsaBand:
+    return _native.PsaBand(int(n), int(kl), int(ku), None)
+
+
+def workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
+                    opts: Optional[LanczosOpts] = None) -> int:
+    lib = _native.load()
+    o = (opts or LanczosOpts())._c()
+    out = ctypes.c_size_t()
+    _native.check(lib.psa_workspace_bytes(ctypes.byref(_band_shape(n, kl, ku)), ctypes.byref(o),
+                                          int(points_in_flight), ctypes.byref(out)), "psa_workspace_bytes")
+    return int(out.value)
+
+
+def default_points_in_flight(npoints: int) -> int:
+    lib = _native.load()
+    out = ctypes.c_int64()
+    _native.check(lib.psa_default_points_in_flight(int(npoints), ctypes.byref(out)),
+                  "psa_default_points_in_flight")
+    return int(out.value)
+
+
+class Workspace:
+    """Reusable device scratch for sigma_min (a torch uint8 buffer, 256-byte aligned)."""
+
+    def __init__(self, n: int, kl: int, ku: int, points_in_flight: int,
+                 opts: Optional[LanczosOpts] = None, device=None):
+        import torch
+        self.nbytes = workspace_bytes(n, kl, ku, points_in_flight, opts)
+        self.buffer = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buffer.data_ptr()
+        self.offset = (-base) % 256
+        self.ptr = base + self.offset
+
+    def fits(self, n: int, kl: int, ku: int, points: int, opts: Optional[LanczosOpts]) -> bool:
+        return workspace_bytes(n, kl, ku, min(points, 32), opts) <= self.nbytes
+
+
+def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), idx=None,
+              opts: Optional[LanczosOpts] = None, workspace: Optional[Workspace] = None,
+              points_in_flight: Optional[int] = None, out: Optional[SigmaMinResult] = None,
+              stream=None) -> SigmaMinResult:
+    """sigma_min(zI - A) and epsilon masks on ``grid`` (or at the flat indices ``idx``).
+
+    bands: CUDA complex128 (kl + ku + 1, n), bands[d + kl, i] = A[i, i + d].
+    idx:   optional CUDA int32 tensor of flat grid indices (restricted mode).
+    Asynchronous on ``stream`` (default: torch's current stream).
+    """
+    import torch
+    lib = _native.load()
+    A = _band(bands, kl, ku)
+    n = A.n
+    g = _native.PsaGrid(float(grid.re_min), float(grid.re_max), float(grid.im_min), float(grid.im_max),
+                        int(grid.nx), int(grid.ny))
+    dev = bands.device
+    npts = grid.npoints if idx is None else int(idx.numel())
+    if idx is not None:
+        if idx.dtype != torch.int32 or not idx.is_cuda or not idx.is_contiguous():
+            raise TypeError("idx must be a contiguous CUDA int32 tensor")
+    o = opts or LanczosOpts()
+    if workspace is None:
+        pif = points_in_flight or default_points_in_flight(max(npts, 1))
+        workspace = Workspace(n, kl, ku, pif, o, device=dev)
+    elif points_in_flight is not None:
+        raise ValueError("pass either workspace or points_in_flight")
+    if out is None:
+        shape = (grid.ny, grid.nx)
+        out = SigmaMinResult(torch.empty(shape, dtype=torch.float64, device=dev),
+                             torch.empty(shape, dtype=torch.int32, device=dev),
+                             torch.empty(shape, dtype=torch.int8, device=dev),
+                             torch.empty(shape, dtype=torch.int32, device=dev))
+    eps_arr = (ctypes.c_double * max(len(eps), 1))(*[float(e) for e in eps])
+    idx_ptr = None
+    if idx is not None:
+        # an empty list is still a list (restricted mode with no points), never NULL
+        idx_ptr = idx.data_ptr() if idx.numel() > 0 else workspace.ptr
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = lib.psa_sigma_min(ctypes.byref(A), ctypes.byref(g), eps_arr, len(eps),
+                           idx_ptr, npts if idx is not None else 0,
+                           out.sigma.data_ptr(), out.mask.data_ptr(), out.status.data_ptr(),
+                           out.steps.data_ptr(), ctypes.byref(o._c()), workspace.ptr, workspace.nbytes,
+                           s.cuda_stream)
+    _native.check(rc, "psa_sigma_min")
+    return out
+
+
+def probe_dfma_rate(iters: int = 4096, stream=None) -> float:
+    """Measured DFMA lane-operations per second of the current device (synchronises)."""
+    import torch
+    lib = _native.load()
+    out = ctypes.c_double()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _native.check(lib.psa_probe_dfma_rate(int(iters), ctypes.byref(out), s.cuda_stream), "psa_probe_dfma_rate")
+    return float(out.value)

@@ -1,0 +1,98 @@
+"""ctypes declarations of the libpsa C ABI (include/psa.h). Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+PSA_OK = 0
+PSA_EINVAL = -1
+PSA_EWORKSPACE = -2
+PSA_ECUDA = -3
+PSA_EUNSUPPORTED = -4
+
+PT_OK, PT_SINGULAR, PT_NOT_CONVERGED, PT_NONFINITE, PT_NOT_EVALUATED, PT_UNDERFLOW = 0, 1, 2, 3, 4, 5
+
+#: every symbol include/psa.h declares
+EXPORTS = (
+    "psa_version",
+    "psa_strerror",
+    "psa_default_opts",
+    "psa_workspace_bytes",
+    "psa_default_points_in_flight",
+    "psa_sigma_min",
+    "psa_probe_dfma_rate",
+)
+
+
+class PsaBand(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kl", ctypes.c_int32), ("ku", ctypes.c_int32),
+                ("bands", ctypes.c_void_p)]
+
+
+class PsaGrid(ctypes.Structure):
+    _fields_ = [("re_min", ctypes.c_double), ("re_max", ctypes.c_double),
+                ("im_min", ctypes.c_double), ("im_max", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+class PsaLanczosOpts(ctypes.Structure):
+    _fields_ = [("k_min", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class PsaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpsa.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpsa.so not found at {path}: build it first "
+                               "(python -m paper_2605_04550_gb300.build)")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.psa_version.restype = ctypes.c_int
+        lib.psa_version.argtypes = []
+        lib.psa_strerror.restype = ctypes.c_char_p
+        lib.psa_strerror.argtypes = [ctypes.c_int]
+        lib.psa_default_opts.restype = PsaLanczosOpts
+        lib.psa_default_opts.argtypes = []
+        lib.psa_workspace_bytes.restype = ctypes.c_int
+        lib.psa_workspace_bytes.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaLanczosOpts), i64,
+                                            ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_default_points_in_flight.restype = ctypes.c_int
+        lib.psa_default_points_in_flight.argtypes = [i64, ctypes.POINTER(i64)]
+        lib.psa_sigma_min.restype = ctypes.c_int
+        lib.psa_sigma_min.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaGrid),
+                                      ctypes.POINTER(dbl), i32, vp, i64, vp, vp, vp, vp,
+                                      ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
+        lib.psa_probe_dfma_rate.restype = ctypes.c_int
+        lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().psa_strerror(code).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "unknown"
+
+
+def check(code: int, what: str) -> None:
+    if code != PSA_OK:
+        raise PsaError(code, what)

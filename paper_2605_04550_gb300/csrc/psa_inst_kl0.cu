@@ -1,0 +1,6 @@
+// Instantiations of the sigma_min kernel for kl = 0 and ku = 0 .. 8.
+#include "psa_kernel.cuh"
+
+namespace psa {
+launch_fn launcher_kl0(int ku) { return launcher_for_ku<0>(ku); }
+}  // namespace psa

@@ -1,0 +1,525 @@
+// psa_kernel.cuh -- the sigma_min(zI - A) kernel for one compile-time band shape.
+//
+// One thread evaluates one grid point; the 32 lanes of a warp hold 32
+// neighbouring points of the grid and run the same instruction stream (same
+// n, kl, ku), so every FP64 instruction does 32 lanes of useful work until a
+// lane's Lanczos process stops. FP64 is the bound on GB300 (about 2 DFMA per
+// SM per clock against 128 FFMA), so the code is arranged to issue as few
+// FP64 instructions per point as the method allows:
+//   * complex multiply-adds are written as 4 explicit fused multiply-adds;
+//   * pivot comparisons, scale exponents and the Sturm sign test use integer
+//     operations on the bit patterns;
+//   * the reciprocal of each pivot is formed once in the factorisation, so the
+//     solves multiply instead of divide;
+//   * the Lanczos dot products and vector updates ride along the triangular
+//     sweeps that produce their operands (four sweeps per step, no extra pass).
+//
+// Per point (paper Sec. 2.1: sigma_min(z) = sigma_n(zI - A); Sec. 2,
+// Definition "Pseudospectrum"):
+//   1. B = zI - A is factored by Gaussian elimination with partial pivoting
+//      inside the band (pivot = largest |Re| + |Im| of rows j..j+kl, first on
+//      ties), with a (kl+1) x (kl+ku+1) register window sliding down the band.
+//   2. Lanczos on H' = (B B^*)^{-1} / 2^(2 e1): step k solves B x = u_k
+//      (interchanges + L forward, U backward), rescales x by a power of two,
+//      solves B^* y = x (U^* forward, L^* backward + interchanges), and forms
+//      w_k = H' q_k - beta_{k-1} q_{k-1}, alpha_k = Re <q_k, w_k>,
+//      u_{k+1} = w_k - alpha_k q_k, beta_k = |u_{k+1}|.
+//   3. theta_k = lambda_max(T_k) by Newton's method on the characteristic
+//      polynomial of T_k from above (monotone, warm-started at the previous
+//      Ritz value); stop when theta_k - theta_{k-1} <= tol * theta_k, at
+//      beta_k = 0 or at k_max. sigma = 2^(-e1) / sqrt(theta_k). A value that
+//      leaves the double range (|B^{-1}| > ~1e308) ends the point with
+//      status UNDERFLOW and sigma = 0.
+//   4. Mask bit l = (sigma <= eps_l) (paper Sec. 2.1, Eq. (sensitive_zone)).
+//
+// Workspace per slot (one slot per thread): every array is [row][P] so that a
+// warp's 32 accesses to one row are 32 consecutive 16-byte values.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "psa_internal.h"
+
+namespace psa {
+namespace dev {
+
+// ------------------------------------------------------------ complex FP64
+// acc - a * b
+__device__ __forceinline__ double2 c_sub_mul(double2 acc, double2 a, double2 b)
+{
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// acc - conj(a) * b
+__device__ __forceinline__ double2 c_sub_conjmul(double2 acc, double2 a, double2 b)
+{
+    return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// a * b
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 c_mul_conj(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -(a.x * b.y)));
+}
+
+// Bit-pattern helpers (integer pipe).
+__device__ __forceinline__ unsigned long long abs_bits(double d)
+{
+    return static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ int exp_field(double d) { return (__double2hiint(d) >> 20) & 0x7ff; }
+// 2^e for e in [-1022, 1023], exact.
+__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// 1 / a by Smith's scaled formula (R. L. Smith, "Algorithm 116: Complex
+// division", CACM 5(8), 1962): with |p| >= |q| the larger and smaller of
+// |Re a|, |Im a|, r = q / p, d = p + q r, and 1/a = (1 - i r) / d or (r - i) / d.
+__device__ __forceinline__ double2 c_rcp(double2 a)
+{
+    const bool re_big = abs_bits(a.x) >= abs_bits(a.y);
+    const double pbig = re_big ? a.x : a.y;
+    const double qsml = re_big ? a.y : a.x;
+    const double r = qsml / pbig;
+    const double d = fma(qsml, r, pbig);
+    const double id = 1.0 / d;
+    const double rid = r * id;
+    return re_big ? make_double2(id, -rid) : make_double2(rid, -id);
+}
+
+// SplitMix64 output number c for `seed` (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long c)
+{
+    unsigned long long z = seed + (c + 1ULL) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------- Ritz value
+// Characteristic polynomial p_k(x) = det(xI - T_k) of the Lanczos tridiagonal
+// (alpha_i = Ta[i*P], beta_i^2 = Tb[i*P]) and its derivative by the three-term
+// recurrence, rescaled by powers of two; returns true when every p_i(x) > 0,
+// i.e. x lies above every eigenvalue of T_k (Sturm).
+__device__ __forceinline__ bool charpoly(const double *Ta, const double *Tb, int64_t P, int k, double x,
+                                         double &pk, double &dpk)
+{
+    double p = x - Ta[0], pp = 1.0, dp = 1.0, dpp = 0.0;
+    int neg = __double2hiint(p);  // sign bit collects any p_i <= 0 (zero checked below)
+    bool zero = (p == 0.0);
+    for (int i = 1; i < k; ++i) {
+        const double a = Ta[(int64_t)i * P];
+        const double b2 = Tb[(int64_t)(i - 1) * P];
+        const double tt = x - a;
+        const double pn = fma(tt, p, -(b2 * pp));
+        const double dpn = fma(tt, dp, fma(-b2, dpp, p));
+        pp = p; p = pn; dpp = dp; dp = dpn;
+        neg |= __double2hiint(p);
+        zero |= (__double_as_longlong(p) << 1) == 0;
+        const int e = exp_field(p);
+        if (e > 1023 + 480 || (e < 1023 - 480 && e != 0)) {
+            const double s = pow2i(1023 - e);
+            p *= s; pp *= s; dp *= s; dpp *= s;
+        }
+    }
+    pk = p;
+    dpk = dp;
+    return neg >= 0 && !zero;
+}
+
+// Largest eigenvalue of T_k from the Gershgorin upper bound (no previous Ritz
+// value known): Newton from above, lower bound max_i alpha_i.
+__device__ __forceinline__ double ritz_top_cold(const double *Ta, const double *Tb, int64_t P, int k)
+{
+    double hi = -1.7e308, lo = -1.7e308, bprev = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double a = Ta[(int64_t)i * P];
+        const double b = (i < k - 1) ? sqrt(Tb[(int64_t)i * P]) : 0.0;
+        hi = fmax(hi, a + bprev + b);
+        lo = fmax(lo, a);
+        bprev = b;
+    }
+    double pk, dpk, x = hi;
+    (void)charpoly(Ta, Tb, P, k, x, pk, dpk);
+    for (int it = 0; it < 200; ++it) {
+        const double d = pk / dpk;
+        double xn = x - d;
+        if (!(xn >= lo)) xn = lo;
+        const bool done = !(fabs(d) > fabs(x) * 0x1.0p-51) || xn == x;
+        x = xn;
+        if (done) break;
+        (void)charpoly(Ta, Tb, P, k, x, pk, dpk);
+    }
+    return x;
+}
+
+// Largest eigenvalue of T_k, k >= 2, given theta_prev = lambda_max(T_{k-1}),
+// its last increment dprev, alpha_k and beta_{k-1}^2. Newton from above on
+// p_k is monotone; the start is the first of a few trial points above
+// theta_prev that the Sturm test accepts, else the Weyl bound
+// max(theta_prev, alpha_k) + beta_{k-1}.
+__device__ __forceinline__ double ritz_top(const double *Ta, const double *Tb, int64_t P, int k,
+                                           double theta_prev, double dprev, double alpha_k, double b2)
+{
+    double pk, dpk;
+    double x = 0.0;
+    bool ok = false;
+    double step = fmax(2.0 * dprev, fabs(theta_prev) * 0x1.0p-40);
+    for (int m = 0; m < 4 && !ok; ++m) {
+        x = theta_prev + step;
+        ok = charpoly(Ta, Tb, P, k, x, pk, dpk);
+        step *= 16.0;
+    }
+    if (!ok) {
+        x = fmax(theta_prev, alpha_k) + sqrt(b2);
+        (void)charpoly(Ta, Tb, P, k, x, pk, dpk);
+    }
+    for (int it = 0; it < 64; ++it) {
+        const double d = pk / dpk;
+        double xn = x - d;
+        if (!(xn >= theta_prev)) xn = theta_prev;  // interlacing: theta_k >= theta_{k-1}
+        const bool done = !(fabs(d) > x * 0x1.0p-51) || xn == x;
+        x = xn;
+        if (done) break;
+        (void)charpoly(Ta, Tb, P, k, x, pk, dpk);
+    }
+    return x;
+}
+
+// ------------------------------------------------------------------ kernel
+template <int KL, int KU>
+__global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
+{
+    constexpr int KW = KL + KU;        // superdiagonals of U after fill-in
+    constexpr int S = 2 * KL + KU + 1; // factor values per row: 1/U_jj, U_{j,j+1..j+KW}, l_{j+1..j+KL}
+    const int64_t P = p.P;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = p.n;
+    const int64_t ngrid = (int64_t)p.nx * p.ny;
+
+    double2 *const F = p.F + t;
+    uint8_t *const piv = p.piv + t;
+    double2 *const Va = p.Va + t;   // q_{k-1} -> q_k
+    double2 *const Vb = p.Vb + t;   // u_k (= beta_{k-1} q_k) -> w_k
+    double2 *const Vx = p.Vx + t;   // solve work vector
+    double *const Ta = p.Ta + t;
+    double *const Tb = p.Tb + t;
+    const int64_t SP = (int64_t)S * P;
+    const bool bad_input = p.flags[0] != 0;
+
+    for (int64_t base = 0; base < p.npts; base += P) {
+        const int64_t pt = base + t;
+        int64_t flat = -1;
+        if (pt < p.npts) {
+            flat = p.idx ? (int64_t)p.idx[pt] : pt;
+            if (flat >= ngrid) flat = -1;
+        }
+        if (flat >= 0) {
+            const int gi = (int)(flat / p.nx);
+            const int gj = (int)(flat - (int64_t)gi * p.nx);
+            const double zr = fma((double)gj, p.hx, p.re_min);
+            const double zi = fma((double)gi, p.hy, p.im_min);
+
+            // ---------------- 1. banded LU with partial pivoting
+            double2 W[KL + 1][KW + 1];
+#pragma unroll
+            for (int r = 0; r <= KL; ++r)
+#pragma unroll
+                for (int c = 0; c <= KW; ++c) {
+                    const int d = c - r;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (d >= -KL && d <= KU && r < n && c < n) {
+                        const double2 a = __ldg(&p.bands[(int64_t)(d + KL) * n + r]);
+                        v = (d == 0) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+                    }
+                    W[r][c] = v;
+                }
+            bool singular = false;
+            for (int j = 0; j < (bad_input ? 0 : n); ++j) {
+                int pr = 0;
+                unsigned long long best = abs_bits(fabs(W[0][0].x) + fabs(W[0][0].y));
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) {
+                    const unsigned long long v = abs_bits(fabs(W[r][0].x) + fabs(W[r][0].y));
+                    if (v > best) { best = v; pr = r; }
+                }
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) {
+                    const bool s = (pr == r);
+#pragma unroll
+                    for (int c = 0; c <= KW; ++c) {
+                        const double2 a = W[0][c], b = W[r][c];
+                        W[0][c] = s ? b : a;
+                        W[r][c] = s ? a : b;
+                    }
+                }
+                if (best == 0ULL) { singular = true; break; }
+                const double2 rp = c_rcp(W[0][0]);
+                double2 *const Fj = F + (int64_t)j * SP;
+                Fj[0] = rp;
+#pragma unroll
+                for (int c = 1; c <= KW; ++c) Fj[(int64_t)c * P] = W[0][c];
+                if (KL > 0) piv[(int64_t)j * P] = (uint8_t)pr;
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) {
+                    const double2 l = c_mul(W[r][0], rp);
+                    Fj[(int64_t)(KW + r) * P] = l;
+#pragma unroll
+                    for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < KL; ++r) {
+#pragma unroll
+                    for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
+                    W[r][KW] = make_double2(0.0, 0.0);
+                }
+                // next row i = j + 1 + KL, columns j+1 .. j+1+KW: d = c - KL
+                const int i = j + 1 + KL;
+#pragma unroll
+                for (int c = 0; c <= KW; ++c) {
+                    const int col = j + 1 + c;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (i < n && col < n) {
+                        const double2 a = __ldg(&p.bands[(int64_t)c * n + i]);
+                        v = (c == KL) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+                    }
+                    W[KL][c] = v;
+                }
+            }
+
+            double sigma = 0.0;
+            int status = bad_input ? 3 : 1;  // NONFINITE input, else SINGULAR
+            int ksteps = 0;
+            if (!singular && !bad_input) {
+                // ---------------- 2. Lanczos on H'
+                double alpha = 0.0, theta = 0.0, theta_prev = 0.0, dprev = 0.0;
+                int e1 = 0;
+                int kth = 0;  // step whose Ritz value `theta` holds
+                const int kmax = p.k_max;
+                const int kr0 = max(1, min(p.k_min, kmax) - 1);  // first step whose Ritz value is needed
+                const int kc0 = max(2, p.k_min);                 // first step with a stopping test
+                status = 2;  // NOT_CONVERGED
+                for (int k = 1;; ++k) {
+                    const bool first = (k == 1);
+                    // (a) u_k = w_{k-1} - alpha_{k-1} q_{k-1} (q_1 at k = 1); |u_k|^2; L forward
+                    double b2 = 0.0;
+                    {
+                        double2 X[KL + 1];
+                        auto make_u = [&](int ii) -> double2 {
+                            double2 u;
+                            if (first) {
+                                u = __ldg(&p.q1[ii]);
+                            } else {
+                                const double2 w = Vb[(int64_t)ii * P];
+                                const double2 q = Va[(int64_t)ii * P];
+                                u = make_double2(fma(-alpha, q.x, w.x), fma(-alpha, q.y, w.y));
+                            }
+                            b2 = fma(u.x, u.x, fma(u.y, u.y, b2));
+                            Vb[(int64_t)ii * P] = u;
+                            return u;
+                        };
+#pragma unroll
+                        for (int r = 0; r < KL; ++r) X[r] = (r < n) ? make_u(r) : make_double2(0.0, 0.0);
+                        for (int j = 0; j < n; ++j) {
+                            X[KL] = (j + KL < n) ? make_u(j + KL) : make_double2(0.0, 0.0);
+                            if (KL > 0) {
+                                const int pj = piv[(int64_t)j * P];
+                                const double2 *Fj = F + (int64_t)j * SP;
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) {
+                                    const bool s = (pj == r);
+                                    const double2 a = X[0], b = X[r];
+                                    X[0] = s ? b : a;
+                                    X[r] = s ? a : b;
+                                }
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) X[r] = c_sub_mul(X[r], Fj[(int64_t)(KW + r) * P], X[0]);
+                            }
+                            Vx[(int64_t)j * P] = X[0];
+#pragma unroll
+                            for (int r = 0; r < KL; ++r) X[r] = X[r + 1];
+                        }
+                    }
+                    if (!first) {
+                        Tb[(int64_t)(k - 2) * P] = b2;  // beta_{k-1}^2 completes T_{k-1}
+                        if (b2 == 0.0) { status = 0; break; }  // Krylov space exhausted: theta exact
+                    }
+                    if (!(b2 <= 1.7e308)) { status = 5; break; }  // overflow: sigma below range
+                    const double beta = sqrt(b2);
+                    const double invb = 1.0 / beta;
+
+                    // (b) U x = Vx backward; x_j = (Vx_j - sum U_{j,j+c} x_{j+c}) / U_jj
+                    int emax = 0;
+                    {
+                        double2 Y[KW + 1];
+#pragma unroll
+                        for (int c = 0; c <= KW; ++c) Y[c] = make_double2(0.0, 0.0);
+                        for (int j = n - 1; j >= 0; --j) {
+                            const double2 *Fj = F + (int64_t)j * SP;
+                            double2 acc = Vx[(int64_t)j * P];
+#pragma unroll
+                            for (int c = 1; c <= KW; ++c) acc = c_sub_mul(acc, Fj[(int64_t)c * P], Y[c]);
+                            const double2 x = c_mul(acc, Fj[0]);
+                            emax = max(emax, max(exp_field(x.x), exp_field(x.y)));
+                            Vx[(int64_t)j * P] = x;
+#pragma unroll
+                            for (int c = KW; c >= 2; --c) Y[c] = Y[c - 1];
+                            if (KW >= 1) Y[1] = x;
+                        }
+                    }
+                    if (emax >= 2047) { status = 5; break; }
+                    const int es = clampi(emax - 1023, -1000, 1000);
+                    if (first) e1 = es;
+                    const double sc = pow2i(-es);
+
+                    // (d) U^* t = x * 2^-es forward, accumulators for rows i..i+KW
+                    {
+                        double2 Acc[KW + 1];
+#pragma unroll
+                        for (int c = 0; c < KW; ++c) {
+                            double2 v = make_double2(0.0, 0.0);
+                            if (c < n) { v = Vx[(int64_t)c * P]; v.x *= sc; v.y *= sc; }
+                            Acc[c] = v;
+                        }
+                        for (int i = 0; i < n; ++i) {
+                            double2 v = make_double2(0.0, 0.0);
+                            if (i + KW < n) { v = Vx[(int64_t)(i + KW) * P]; v.x *= sc; v.y *= sc; }
+                            Acc[KW] = v;
+                            const double2 *Fi = F + (int64_t)i * SP;
+                            const double2 tt = c_mul_conj(Acc[0], Fi[0]);
+                            Vx[(int64_t)i * P] = tt;
+#pragma unroll
+                            for (int c = 1; c <= KW; ++c) Acc[c] = c_sub_conjmul(Acc[c], Fi[(int64_t)c * P], tt);
+#pragma unroll
+                            for (int c = 0; c < KW; ++c) Acc[c] = Acc[c + 1];
+                        }
+                    }
+
+                    // (e) L^* backward with interchanges; as each y_i becomes final:
+                    //     q_i = u_i / beta_{k-1}, w_i = f y_i - beta_{k-1} q_{k-1,i}, alpha += Re(conj(q_i) w_i)
+                    const double f = (invb * pow2i(clampi(es - e1, -1022, 1023))) * pow2i(clampi(-e1, -1022, 1023));
+                    double asum = 0.0;
+                    {
+                        auto emit = [&](int ii, double2 y) {
+                            const double2 u = Vb[(int64_t)ii * P];
+                            const double2 q = make_double2(u.x * invb, u.y * invb);
+                            double2 w;
+                            if (first) {
+                                w = make_double2(f * y.x, f * y.y);
+                            } else {
+                                const double2 qp = Va[(int64_t)ii * P];
+                                w = make_double2(fma(f, y.x, -(beta * qp.x)), fma(f, y.y, -(beta * qp.y)));
+                            }
+                            asum = fma(q.x, w.x, fma(q.y, w.y, asum));
+                            Va[(int64_t)ii * P] = q;
+                            Vb[(int64_t)ii * P] = w;
+                        };
+                        double2 T[KL + 1];
+#pragma unroll
+                        for (int r = 0; r <= KL; ++r) T[r] = make_double2(0.0, 0.0);
+                        for (int j = n - 1; j >= 0; --j) {
+#pragma unroll
+                            for (int r = KL; r >= 1; --r) T[r] = T[r - 1];
+                            T[0] = Vx[(int64_t)j * P];
+                            if (KL > 0) {
+                                const double2 *Fj = F + (int64_t)j * SP;
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) T[0] = c_sub_conjmul(T[0], Fj[(int64_t)(KW + r) * P], T[r]);
+                                const int pj = piv[(int64_t)j * P];
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) {
+                                    const bool s = (pj == r);
+                                    const double2 a = T[0], b = T[r];
+                                    T[0] = s ? b : a;
+                                    T[r] = s ? a : b;
+                                }
+                                if (j + KL < n) emit(j + KL, T[KL]);
+                            } else {
+                                emit(j, T[0]);
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < KL; ++r)
+                            if (r < n) emit(r, T[r]);
+                    }
+                    alpha = asum;
+                    Ta[(int64_t)(k - 1) * P] = alpha;
+                    ksteps = k;
+
+                    // ---------------- 3. Ritz value and stopping test
+                    if (k >= kr0) {
+                        double th;
+                        if (k == 1) th = alpha;
+                        else if (kth == k - 1) th = ritz_top(Ta, Tb, P, k, theta, dprev, alpha, b2);
+                        else th = ritz_top_cold(Ta, Tb, P, k);
+                        const bool have_prev = (kth == k - 1);
+                        theta_prev = theta;
+                        theta = th;
+                        kth = k;
+                        dprev = have_prev ? theta - theta_prev : 0.0;
+                        if (k >= kc0 && have_prev && theta - theta_prev <= p.tol * theta) { status = 0; break; }
+                    }
+                    if (k >= kmax) break;
+                }
+                if (status != 5 && kth != ksteps && ksteps >= 1) {
+                    theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, P, ksteps);
+                    kth = ksteps;
+                }
+                if (status != 5) {
+                    if (!(theta > 0.0) || !(theta <= 1.7e308)) {
+                        status = 5;
+                    } else {
+                        sigma = (1.0 / sqrt(theta)) * pow2i(clampi(-e1, -1022, 1023));
+                    }
+                }
+                if (status == 5) sigma = 0.0;
+            }
+
+            // ---------------- 4. outputs
+            p.sigma[flat] = sigma;
+            if (p.mask) {
+                uint32_t bits = 0;
+                const unsigned long long sb = abs_bits(sigma);
+                for (int l = 0; l < p.n_eps; ++l)
+                    bits |= (sb <= abs_bits(p.eps[l]) ? 1u : 0u) << l;
+                p.mask[flat] = bits;
+            }
+            if (p.status) p.status[flat] = (int8_t)status;
+            if (p.steps) p.steps[flat] = ksteps;
+        }
+    }
+}
+
+template <int KL, int KU>
+cudaError_t launch_sigma_min(const KParams &p, cudaStream_t stream)
+{
+    const int threads = (p.P % kThreads == 0) ? kThreads : 32;
+    const unsigned blocks = (unsigned)(p.P / threads);
+    k_sigma_min<KL, KU><<<blocks, threads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace dev
+
+// Table of launchers for one kl and ku = 0 .. kMaxKU.
+template <int KL>
+launch_fn launcher_for_ku(int ku)
+{
+    switch (ku) {
+    case 0: return &dev::launch_sigma_min<KL, 0>;
+    case 1: return &dev::launch_sigma_min<KL, 1>;
+    case 2: return &dev::launch_sigma_min<KL, 2>;
+    case 3: return &dev::launch_sigma_min<KL, 3>;
+    case 4: return &dev::launch_sigma_min<KL, 4>;
+    case 5: return &dev::launch_sigma_min<KL, 5>;
+    case 6: return &dev::launch_sigma_min<KL, 6>;
+    case 7: return &dev::launch_sigma_min<KL, 7>;
+    case 8: return &dev::launch_sigma_min<KL, 8>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace psa

@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/psa.h declares, sizes its workspace as documented and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_04550_gb300 import _native
+from paper_2605_04550_gb300.build import ROOT, build_library
+
+HEADER = os.path.join(ROOT, "include", "psa.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_library()
+    return _native.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(psa_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared_functions() == sorted(_native.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_strerror(lib):
+    assert lib.psa_version() >= 100
+    for code in (0, -1, -2, -3, -4):
+        assert lib.psa_strerror(code)
+    assert b"unsupported" in lib.psa_strerror(-4)
+
+
+def test_default_opts(lib):
+    o = lib.psa_default_opts()
+    assert (o.k_min, o.k_max, o.tol, o.seed) == (2, 1000, 1e-13, 0)
+
+
+def _ws(lib, n, kl, ku, P, kmax=1000):
+    out = ctypes.c_size_t()
+    o = _native.PsaLanczosOpts(2, kmax, 1e-13, 0)
+    rc = lib.psa_workspace_bytes(ctypes.byref(_native.PsaBand(n, kl, ku, None)), ctypes.byref(o), P,
+                                 ctypes.byref(out))
+    return rc, out.value
+
+
+def test_workspace_bytes_layout(lib):
+    rc, b = _ws(lib, 2000, 2, 5, 128)
+    assert rc == 0
+    n, S, P, kmax = 2000, 10, 128, 1000
+    expect = 16 * n * S * P + n * P + 3 * 16 * n * P + 2 * 8 * kmax * P + 16 * n
+    assert expect <= b <= expect + 10 * 256
+    # rounded up to a multiple of 32 points
+    assert _ws(lib, 2000, 2, 5, 97)[1] == _ws(lib, 2000, 2, 5, 128)[1]
+
+
+@pytest.mark.parametrize("n,kl,ku,P", [(0, 0, 0, 32), (5, 5, 0, 32), (5, 0, 5, 32), (5, -1, 0, 32), (5, 1, 1, 0)])
+def test_workspace_bytes_rejects(lib, n, kl, ku, P):
+    assert _ws(lib, n, kl, ku, P)[0] == _native.PSA_EINVAL
+
+
+def _call(lib, *, n=10, kl=1, ku=1, bands=1 << 20, grid=(-1.0, 1.0, -1.0, 1.0, 4, 4), eps=(0.1,),
+          n_eps=None, idx=None, n_idx=0, sigma=1 << 21, opts=None, ws=1 << 22, ws_bytes=1 << 30):
+    A = _native.PsaBand(n, kl, ku, bands)
+    g = _native.PsaGrid(*grid)
+    e = (ctypes.c_double * max(len(eps), 1))(*eps)
+    o = opts if opts is not None else _native.PsaLanczosOpts(2, 100, 1e-13, 0)
+    return lib.psa_sigma_min(ctypes.byref(A), ctypes.byref(g), e, len(eps) if n_eps is None else n_eps,
+                             idx, n_idx, sigma, None, None, None, ctypes.byref(o), ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=0), _native.PSA_EINVAL),
+    (dict(kl=10), _native.PSA_EINVAL),
+    (dict(bands=None), _native.PSA_EINVAL),
+    (dict(sigma=None), _native.PSA_EINVAL),
+    (dict(grid=(1.0, -1.0, -1.0, 1.0, 4, 4)), _native.PSA_EINVAL),
+    (dict(grid=(-1.0, 1.0, -1.0, 1.0, 0, 4)), _native.PSA_EINVAL),
+    (dict(grid=(-1.0, float("nan"), -1.0, 1.0, 4, 4)), _native.PSA_EINVAL),
+    (dict(grid=(-1.0, 1.0, -1.0, 1.0, 65536, 65536)), _native.PSA_EINVAL),
+    (dict(eps=(0.0,)), _native.PSA_EINVAL),
+    (dict(eps=(-1e-3,)), _native.PSA_EINVAL),
+    (dict(eps=(float("inf"),)), _native.PSA_EINVAL),
+    (dict(n_eps=33), _native.PSA_EINVAL),
+    (dict(n_idx=5, idx=None), _native.PSA_EINVAL),
+    (dict(n_idx=-1), _native.PSA_EINVAL),
+    (dict(opts=_native.PsaLanczosOpts(5, 4, 1e-13, 0)), _native.PSA_EINVAL),
+    (dict(opts=_native.PsaLanczosOpts(2, 0, 1e-13, 0)), _native.PSA_EINVAL),
+    (dict(opts=_native.PsaLanczosOpts(2, 70000, 1e-13, 0)), _native.PSA_EINVAL),
+    (dict(opts=_native.PsaLanczosOpts(2, 10, -1.0, 0)), _native.PSA_EINVAL),
+    (dict(n=20, kl=5, ku=1), _native.PSA_EUNSUPPORTED),
+    (dict(n=20, kl=1, ku=9), _native.PSA_EUNSUPPORTED),
+    (dict(ws=None), _native.PSA_EWORKSPACE),
+    (dict(ws=(1 << 22) + 8), _native.PSA_EWORKSPACE),
+    (dict(ws_bytes=1000), _native.PSA_EWORKSPACE),
+])
+def test_sigma_min_rejects_bad_arguments(lib, kw, code):
+    # every rejection happens on the host, before any device call
+    assert _call(lib, **kw) == code

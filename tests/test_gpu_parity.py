@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Parity rule (tests/parity.py): |sigma - sigma_ref| <= 1e-10 sigma_ref + 1e-13 |zI - A|_1
+per point; mask bits identical except within max(1e-9 eps, 1e-13 |zI - A|_1) of a
+level; statuses SINGULAR / NONFINITE / NOT_EVALUATED identical. The oracle runs to
+convergence (tol 1e-15); the library runs its default converged mode (tol 1e-13).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2605_04550_gb300 as psa
+from paper_2605_04550_gb300 import inputs
+from tests.parity import band_norm1, check_masks, check_sigma
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _gpu(bands, kl, ku, grid, eps=(), idx=None, opts=None, **kw):
+    b = torch.as_tensor(np.ascontiguousarray(bands), device=DEV)
+    i = None if idx is None else torch.as_tensor(np.asarray(idx, dtype=np.int32), device=DEV)
+    out = psa.sigma_min(b, kl, ku, grid, eps=eps, idx=i, opts=opts, **kw)
+    torch.cuda.synchronize()
+    return (out.sigma.cpu().numpy().ravel(), out.mask.cpu().numpy().view(np.uint32).ravel(),
+            out.status.cpu().numpy().ravel(), out.steps.cpu().numpy().ravel())
+
+
+def _assert_parity(bands, kl, ku, grid, eps, sig, mask, status, sample=None, **okw):
+    z = oracle.grid_points(grid).ravel()
+    pts = np.arange(z.size) if sample is None else np.asarray(sample)
+    ref, st_ref, _ = oracle.sigma_min_banded(bands, kl, ku, z[pts], **okw)
+    nrm = band_norm1(bands, kl, ku, z[pts])
+    bad, info = check_sigma(sig[pts], ref, nrm)
+    assert not bad.any(), (info, pts[bad][:5], sig[pts][bad][:5], ref[bad][:5])
+    if eps:
+        bad_m, n_excl = check_masks(mask[pts], oracle.masks(ref, eps), ref, nrm, eps)
+        assert not bad_m.any(), (pts[bad_m][:5], n_excl)
+    # SINGULAR and NONFINITE are decided identically; UNDERFLOW (sigma below the double
+    # range) on either side is covered by the sigma rule (both below the floor)
+    for code in (psa.PT_SINGULAR, psa.PT_NONFINITE):
+        np.testing.assert_array_equal(status[pts] == code, st_ref == code)
+    return info
+
+
+# --------------------------------------------------------------- workloads
+def test_grcar_100_full_grid():
+    bands, kl, ku = inputs.grcar(100)
+    grid, eps = inputs.grcar_grid_100(), inputs.EPS_LEVELS_8
+    sig, mask, st, steps = _gpu(bands, kl, ku, grid, eps)
+    info = _assert_parity(bands, kl, ku, grid, eps, sig, mask, st)
+    assert np.all(st == psa.PT_OK)
+    # exact tier: dense SVD (the paper's method) at a sample
+    z = oracle.grid_points(grid).ravel()
+    smp = np.arange(0, z.size, 97)
+    dense = oracle.sigma_min_dense(oracle.band_to_dense(bands, kl, ku), z[smp])
+    bad, info = check_sigma(sig[smp], dense, band_norm1(bands, kl, ku, z[smp]))
+    assert not bad.any(), info
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
+def test_paper_class_full_grid(seed):
+    bands, kl, ku, A = inputs.paper_class(seed)
+    grid = inputs.paper_grid_100()
+    sig, mask, st, _ = _gpu(bands, kl, ku, grid, (0.01,))
+    _assert_parity(bands, kl, ku, grid, (0.01,), sig, mask, st)
+    z = oracle.grid_points(grid).ravel()
+    smp = np.arange(3, z.size, 211)
+    dense = oracle.sigma_min_dense(A, z[smp])
+    bad, info = check_sigma(sig[smp], dense, band_norm1(bands, kl, ku, z[smp]))
+    assert not bad.any(), info
+
+
+def test_toeplitz_ragged_grid():
+    # 37 x 29 = 1073 points: several warps and a ragged tail
+    bands, kl, ku, a = inputs.random_toeplitz(300, 2, 5, seed=0)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 37, 29)
+    eps = inputs.EPS_LEVELS_8
+    sig, mask, st, _ = _gpu(bands, kl, ku, grid, eps)
+    _assert_parity(bands, kl, ku, grid, eps, sig, mask, st)
+
+
+def test_toeplitz_2000_full_size_sampled():
+    """The benchmark's workload (n = 2000, kl = 2, ku = 5, 512 x 512) in the benchmark's
+    launch configuration, checked at 96 sampled points against the oracle."""
+    bands, kl, ku, a = inputs.random_toeplitz(2000, 2, 5, seed=0)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 512, 512)
+    eps = inputs.EPS_LEVELS_8
+    sig, mask, st, steps = _gpu(bands, kl, ku, grid, eps)
+    rng = np.random.default_rng(0)
+    smp = np.sort(rng.choice(grid.npoints, 96, replace=False))
+    _assert_parity(bands, kl, ku, grid, eps, sig, mask, st, sample=smp)
+    assert np.all((st == psa.PT_OK) | (st == psa.PT_UNDERFLOW))
+
+
+@pytest.mark.parametrize("kl,ku", [(kl, ku) for kl in range(5) for ku in range(9)])
+def test_every_band_shape(kl, ku):
+    bands, _, _, a = inputs.random_toeplitz(40, kl, ku, seed=kl * 10 + ku, super_scale=2.0)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 9, 7)
+    sig, mask, st, _ = _gpu(bands, kl, ku, grid, (1e-2,))
+    _assert_parity(bands, kl, ku, grid, (1e-2,), sig, mask, st)
+
+
+# -------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("n,kl,ku", [(1, 0, 0), (2, 1, 1), (2, 0, 1), (3, 2, 2), (3, 2, 0), (5, 4, 4), (9, 4, 8)])
+def test_tiny_orders(n, kl, ku):
+    bands, _, _, a = inputs.random_toeplitz(n, kl, ku, seed=n, super_scale=1.5)
+    grid = inputs.Grid(-3.0, 3.0, -3.0, 3.0, 11, 6)
+    sig, mask, st, _ = _gpu(bands, kl, ku, grid, (0.5, 0.1))
+    _assert_parity(bands, kl, ku, grid, (0.5, 0.1), sig, mask, st)
+    z = oracle.grid_points(grid).ravel()
+    dense = oracle.sigma_min_dense(oracle.band_to_dense(bands, kl, ku), z)
+    bad, info = check_sigma(sig, dense, band_norm1(bands, kl, ku, z))
+    assert not bad.any(), info
+
+
+def test_normal_matrix_closed_form():
+    bands, kl, ku = inputs.hermitian_toeplitz_tridiag(64, 0.3, 0.7 - 0.4j)
+    lam = 0.3 + 2 * abs(0.7 - 0.4j) * np.cos(np.arange(1, 65) * np.pi / 65)
+    grid = inputs.Grid(-2.0, 2.5, -1.0, 1.0, 33, 17)
+    sig, _, _, _ = _gpu(bands, kl, ku, grid)
+    z = oracle.grid_points(grid).ravel()
+    exact = np.array([np.min(np.abs(zz - lam)) for zz in z])
+    bad, info = check_sigma(sig, exact, band_norm1(bands, kl, ku, z), rel=1e-12)
+    assert not bad.any(), info
+
+
+def test_singular_point_and_nonfinite():
+    lam = np.array([0.5 + 0.25j, -1.0, 2.0j, 1.5 - 0.5j])
+    bands = lam.reshape(1, 4).astype(np.complex128)
+    grid = inputs.Grid(0.5, 0.5, 0.25, 0.25, 1, 1)      # z = lam[0] exactly
+    sig, mask, st, _ = _gpu(bands, 0, 0, grid, (1e-3,))
+    assert st[0] == psa.PT_SINGULAR and sig[0] == 0.0 and mask[0] == 1
+    b, kl, ku = inputs.grcar(20)
+    b = b.copy()
+    b[2, 7] = np.nan
+    sig, mask, st, _ = _gpu(b, kl, ku, inputs.Grid(0.0, 1.0, 0.0, 1.0, 4, 2))
+    assert np.all(st == psa.PT_NONFINITE)
+
+
+def test_fixed_step_mode_matches_oracle_fixed():
+    bands, kl, ku = inputs.grcar(100)
+    grid = inputs.grcar_grid_100()
+    sig, _, st, steps = _gpu(bands, kl, ku, grid, opts=psa.LanczosOpts.fixed(20))
+    assert np.all(steps == 20)
+    z = oracle.grid_points(grid).ravel()
+    ref, _, _ = oracle.sigma_min_banded(bands, kl, ku, z, k_min=20, k_max=20, tol=0.0)
+    # same recurrence and start vector, different rounding: agreement is limited by
+    # the Lanczos sensitivity after 20 steps, not by the converged value
+    nrm = band_norm1(bands, kl, ku, z)
+    err = np.abs(sig - ref)
+    assert np.all(err <= 1e-8 * ref + 1e-13 * nrm)
+
+
+# --------------------------------------------------- restricted mode, layout
+def test_restricted_list_is_bitwise_full_grid():
+    bands, kl, ku, a = inputs.random_toeplitz(500, 2, 5, seed=3)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 40, 30)
+    eps = inputs.EPS_LEVELS_8
+    full_s, full_m, full_st, full_k = _gpu(bands, kl, ku, grid, eps)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(grid.npoints, 333, replace=False)).astype(np.int32)
+    idx_shuf = rng.permutation(idx)
+    s, m, st, k = _gpu(bands, kl, ku, grid, eps, idx=idx_shuf)
+    np.testing.assert_array_equal(s[idx], full_s[idx])
+    np.testing.assert_array_equal(m[idx], full_m[idx])
+    np.testing.assert_array_equal(k[idx], full_k[idx])
+    rest = np.setdiff1d(np.arange(grid.npoints), idx)
+    assert np.all(np.isnan(s[rest])) and np.all(m[rest] == 0) and np.all(st[rest] == psa.PT_NOT_EVALUATED)
+
+
+def test_restricted_empty_and_out_of_range():
+    bands, kl, ku = inputs.grcar(50)
+    grid = inputs.Grid(-1, 3, -3, 3, 8, 8)
+    s, m, st, _ = _gpu(bands, kl, ku, grid, (0.1,), idx=np.zeros(0, np.int32))
+    assert np.all(st == psa.PT_NOT_EVALUATED)
+    s2, _, st2, _ = _gpu(bands, kl, ku, grid, (0.1,), idx=np.array([64, 5, 1000, 63], np.int32))
+    assert st2[5] == psa.PT_OK and st2[63] == psa.PT_OK
+    assert np.sum(st2 != psa.PT_NOT_EVALUATED) == 2
+
+
+def test_points_in_flight_do_not_change_results():
+    bands, kl, ku = inputs.grcar(100)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 45, 23)
+    ref = _gpu(bands, kl, ku, grid, (0.1,))
+    for pif in (32, 96, 128, 640):
+        got = _gpu(bands, kl, ku, grid, (0.1,), points_in_flight=pif)
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_power_of_two_scaling_is_bitwise_on_gpu():
+    bands, kl, ku = inputs.grcar(100)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 20, 20)
+    s0 = _gpu(bands, kl, ku, grid)[0]
+    for m in (-5, 7):
+        g2 = inputs.Grid(grid.re_min * 2.0**m, grid.re_max * 2.0**m, grid.im_min * 2.0**m,
+                         grid.im_max * 2.0**m, 20, 20)
+        s2 = _gpu(bands * 2.0**m, kl, ku, g2)[0]
+        np.testing.assert_array_equal(s2, s0 * 2.0**m)
+
+
+def test_transpose_invariance_on_gpu():
+    bands, kl, ku, a = inputs.random_toeplitz(200, 1, 4, seed=5)
+    n = 200
+    bt = np.zeros((kl + ku + 1, n), dtype=np.complex128)
+    for d in range(-ku, kl + 1):
+        for i in range(n):
+            if 0 <= i + d < n:
+                bt[d + ku, i] = bands[-d + kl, i + d]
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 16, 16)
+    s = _gpu(bands, kl, ku, grid)[0]
+    st = _gpu(bt, ku, kl, grid)[0]
+    z = oracle.grid_points(grid).ravel()
+    bad, info = check_sigma(st, s, band_norm1(bands, kl, ku, z))
+    assert not bad.any(), info
+
+
+def test_seed_changes_start_vector_not_result():
+    bands, kl, ku = inputs.grcar(100)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 16, 16)
+    s0 = _gpu(bands, kl, ku, grid)[0]
+    s1 = _gpu(bands, kl, ku, grid, opts=psa.LanczosOpts(seed=12345))[0]
+    z = oracle.grid_points(grid).ravel()
+    bad, info = check_sigma(s1, s0, band_norm1(bands, kl, ku, z))
+    assert not bad.any(), info
