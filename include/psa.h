@@ -44,6 +44,8 @@ extern "C" {
 #define PSA_EWORKSPACE (-2)  /* workspace too small (or NULL) for even one warp of points */
 #define PSA_ECUDA (-3)       /* a CUDA launch or query failed (see cudaGetLastError) */
 #define PSA_EUNSUPPORTED (-4) /* band widths beyond kl <= 4, ku <= 8 */
+#define PSA_ESTATIC (-5)     /* psa_sigma_min_static: the problem needs more scratch than
+                                PSA_STATIC_SCRATCH_BYTES for one warp (32 points) */
 
 /* ----------------------------------------------------- per-point status */
 #define PSA_PT_OK 0             /* converged (or fixed step count completed) */
@@ -151,6 +153,41 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g,
                   double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
                   const psa_lanczos_opts *opts,
                   void *workspace, size_t ws_bytes, void *stream);
+
+/* Size of the fixed device scratch used by psa_sigma_min_static (64 MiB). */
+#define PSA_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* psa_sigma_min for callers that cannot allocate device memory. The paper
+ * has no counterpart: this is a deployment variant of psa_sigma_min.
+ *
+ * Some callers cannot call cudaMalloc or any allocating routine: a host that
+ * hands its GPU memory out once at start-up, a real-time or latency-bound
+ * loop where allocation may block, a sandboxed plugin without allocator
+ * rights. This entry point takes the same arguments as psa_sigma_min except
+ * the workspace: its scratch is one file-scope device array of
+ * PSA_STATIC_SCRATCH_BYTES (64 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits. It allocates nothing and
+ * calls no allocating routine; outputs and inputs remain the caller's.
+ *
+ *  - Set-up: the first call on a device, with that device current, looks up
+ *    the array's device address (cudaGetSymbolAddress) and caches it; make
+ *    that first call before any stream capture.
+ *  - Size limit: the scratch must hold at least one warp of points (see
+ *    psa_workspace_bytes with points_in_flight = 32); larger problems are
+ *    rejected with PSA_ESTATIC and nothing is launched. Within the limit the
+ *    number of points in flight is what fits, so big problems run slower
+ *    than with a large caller workspace.
+ *  - Sharing: every call uses the same array, which keeps the previous
+ *    call's contents (each call clears the parts that must start at zero).
+ *    Calls whose kernels may overlap on the GPU (different streams, or
+ *    several host threads) race on the array: serialise them.
+ * Results are those of psa_sigma_min on the same arguments.
+ * Errors: as psa_sigma_min, plus PSA_ESTATIC. */
+int psa_sigma_min_static(const psa_band *A, const psa_grid *g,
+                         const double *eps, int32_t n_eps,
+                         const int32_t *idx, int64_t n_idx,
+                         double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
+                         const psa_lanczos_opts *opts, void *stream);
 
 /* Measured FP64 throughput of this device: runs a kernel of independent DFMA
  * chains (iters iterations, 8 chains, SM count x 16 warps) on `stream`,

@@ -12,6 +12,8 @@ PSA_EINVAL = -1
 PSA_EWORKSPACE = -2
 PSA_ECUDA = -3
 PSA_EUNSUPPORTED = -4
+PSA_ESTATIC = -5
+STATIC_SCRATCH_BYTES = 64 << 20
 
 PT_OK, PT_SINGULAR, PT_NOT_CONVERGED, PT_NONFINITE, PT_NOT_EVALUATED, PT_UNDERFLOW = 0, 1, 2, 3, 4, 5
 
@@ -23,6 +25,7 @@ EXPORTS = (
     "psa_workspace_bytes",
     "psa_default_points_in_flight",
     "psa_sigma_min",
+    "psa_sigma_min_static",
     "psa_probe_dfma_rate",
 )
 
@@ -80,6 +83,10 @@ def load(path: str | None = None):
         lib.psa_sigma_min.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaGrid),
                                       ctypes.POINTER(dbl), i32, vp, i64, vp, vp, vp, vp,
                                       ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
+        lib.psa_sigma_min_static.restype = ctypes.c_int
+        lib.psa_sigma_min_static.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaGrid),
+                                             ctypes.POINTER(dbl), i32, vp, i64, vp, vp, vp, vp,
+                                             ctypes.POINTER(PsaLanczosOpts), vp]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         _lib = lib

@@ -155,6 +155,7 @@ const char *psa_strerror(int code)
     case PSA_EWORKSPACE: return "workspace too small";
     case PSA_ECUDA: return "CUDA error";
     case PSA_EUNSUPPORTED: return "unsupported band shape (kl <= 4, ku <= 8)";
+    case PSA_ESTATIC: return "problem too large for the static scratch of psa_sigma_min_static";
     default: return "unknown error";
     }
 }

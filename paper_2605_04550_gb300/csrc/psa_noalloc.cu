@@ -1,0 +1,58 @@
+// psa_noalloc.cu -- psa_sigma_min_static: the sigma_min grid evaluation for
+// callers that cannot allocate device memory.
+//
+// Some callers have no way to obtain device scratch: code running inside a
+// host that forbids cudaMalloc after start-up (a memory pool handed out once,
+// a real-time loop, a plugin sandbox), or code that must not allocate while a
+// stream is being captured. For them the scratch that psa_sigma_min takes as
+// `workspace` lives here instead, in one file-scope device array of fixed size
+// that the module carries for as long as the library is loaded.
+//
+// The host may not use the array's name as a device address (in host code it
+// names a host-side stand-in), so the device address is looked up with
+// cudaGetSymbolAddress, once per device with that device current, and cached.
+#include <cuda_runtime.h>
+#include <mutex>
+
+#include "psa.h"
+
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[PSA_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once).
+int static_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSA_ECUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return PSA_ECUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return PSA_OK;
+}
+
+}  // namespace
+
+extern "C" int psa_sigma_min_static(const psa_band *A, const psa_grid *g, const double *eps, int32_t n_eps,
+                                    const int32_t *idx, int64_t n_idx, double *sigma, uint32_t *mask,
+                                    int8_t *status, int32_t *steps, const psa_lanczos_opts *opts, void *stream)
+{
+    // the problem must fit the fixed scratch with at least one warp (32 points) in flight
+    size_t need = 0;
+    const int rc = psa_workspace_bytes(A, opts, 32, &need);
+    if (rc != PSA_OK) return rc;
+    if (need > (size_t)PSA_STATIC_SCRATCH_BYTES) return PSA_ESTATIC;
+    void *scratch = nullptr;
+    const int rs = static_scratch(&scratch);
+    if (rs != PSA_OK) return rs;
+    return psa_sigma_min(A, g, eps, n_eps, idx, n_idx, sigma, mask, status, steps, opts, scratch,
+                         (size_t)PSA_STATIC_SCRATCH_BYTES, stream);
+}
