@@ -50,9 +50,9 @@ WORKLOAD = (f"random banded Toeplitz n={N} kl={KL} ku={KU} (complex N(0,1) coeff
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
-# reduced case for profiler captures: same matrix family, n = 256, one wave of
-# 38,896 points (208 x 187 grid), k_max 300 -> about 2.3 GB of workspace
-SMALL = dict(n=256, nx=208, ny=187, kmax=300)
+# reduced case for profiler captures: same matrix family, n = 256, 384 x 384 grid
+# (about 2.5 waves of points in flight), k_max 300 -> about 3.5 GB of workspace
+SMALL = dict(n=256, nx=384, ny=384, kmax=300)
 
 
 def workload(case: str = "mid"):
@@ -219,7 +219,7 @@ def run_gpu(args):
     npts = grid.npoints
     b_dev = torch.as_tensor(bands, device=dev)
     opts = psa.LanczosOpts(k_min=2, k_max=KMAX if args.case == "mid" else SMALL["kmax"], tol=TOL, seed=0)
-    pif = psa.default_points_in_flight(npts)
+    pif = psa.default_points_in_flight(n, kl, ku, npts)
     wsp = psa.Workspace(n, kl, ku, pif, opts, device=dev)
     out = psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp)
     stream = torch.cuda.current_stream(dev)

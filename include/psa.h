@@ -107,25 +107,29 @@ const char *psa_strerror(int code);
 psa_lanczos_opts psa_default_opts(void);
 
 /* Bytes of device workspace that psa_sigma_min needs to keep
- * `points_in_flight` points in flight at once (rounded up to a multiple of
- * 32). The workspace holds, per point in flight, the pivoted band factor
- * (n * (2kl + ku + 1) complex values and n pivot offsets), three Lanczos
- * vectors and the tridiagonal coefficients (2 * k_max values), plus the
- * shared start vector. Host call, no device work.
+ * `points_in_flight` points in flight at once (rounded up to whole warps of
+ * 32). The workspace holds a 256-byte flag block, the shared start vector
+ * (n complex values) and one block per warp: for each of the n rows the
+ * warp's pivoted band factor (2kl + ku + 1 complex values per point), three
+ * Lanczos vectors and the pivot offsets, then the tridiagonal coefficients
+ * (2 * k_max values per point). Host call, no device work.
  * Errors: PSA_EINVAL for bad A fields (bands pointer may be NULL here),
  * bad opts, points_in_flight < 1 or bytes == NULL. */
 int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts,
                         int64_t points_in_flight, size_t *bytes);
 
-/* Points in flight that fill the current device (SM count x 8 warps x 32),
- * capped at `npoints` rounded up to 32. Host call (queries the device).
- * Errors: PSA_EINVAL (npoints < 1 or out == NULL), PSA_ECUDA. */
-int psa_default_points_in_flight(int64_t npoints, int64_t *out);
+/* Points in flight that fill the current device once with the kernel for
+ * A's band shape (SM count x resident blocks x 128 threads, from the CUDA
+ * occupancy calculator), capped at `npoints` rounded up to 32. Host call.
+ * Errors: PSA_EINVAL (bad A fields, npoints < 1 or out == NULL),
+ * PSA_EUNSUPPORTED, PSA_ECUDA. */
+int psa_default_points_in_flight(const psa_band *A, int64_t npoints, int64_t *out);
 
 /* sigma_min(zI - A) and its epsilon masks over a grid.
  *
  *  A        band matrix (device bands), 1 <= n, 0 <= kl, ku <= n - 1,
- *           kl <= 4, ku <= 8 (else PSA_EUNSUPPORTED).
+ *           kl <= 4, ku <= 8 and n * ((2kl + ku + 4) * 512 + 128) < 2^31
+ *           (else PSA_EUNSUPPORTED).
  *  g        grid; finite bounds with re_min <= re_max, im_min <= im_max;
  *           nx, ny >= 1 and nx * ny <= 2^31 - 1.
  *  eps      HOST array of n_eps levels, 0 <= n_eps <= 32, each finite and > 0.
@@ -143,8 +147,12 @@ int psa_default_points_in_flight(int64_t npoints, int64_t *out);
  *  opts     Lanczos controls (NULL = psa_default_opts()).
  *  workspace, ws_bytes
  *           DEVICE scratch of ws_bytes bytes, 256-byte aligned; its size sets
- *           the number of points in flight (see psa_workspace_bytes); it must
- *           not be used by another call that may run at the same time.
+ *           the number of points in flight (whole warps, at most one full
+ *           occupancy of the device; see psa_workspace_bytes); it must not be
+ *           used by another call that may run at the same time. Warps take
+ *           groups of 32 consecutive points from a counter in the workspace,
+ *           so the assignment of points to warps varies between calls while
+ *           every point's arithmetic, and so its result, does not.
  *  stream   cudaStream_t to launch on.
  * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_EUNSUPPORTED, PSA_ECUDA. */
 int psa_sigma_min(const psa_band *A, const psa_grid *g,

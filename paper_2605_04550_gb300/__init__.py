@@ -85,11 +85,12 @@ def workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
     return int(out.value)
 
 
-def default_points_in_flight(npoints: int) -> int:
+def default_points_in_flight(n: int, kl: int, ku: int, npoints: int) -> int:
+    """Points in flight that fill the device once for this band shape."""
     lib = _native.load()
     out = ctypes.c_int64()
-    _native.check(lib.psa_default_points_in_flight(int(npoints), ctypes.byref(out)),
-                  "psa_default_points_in_flight")
+    _native.check(lib.psa_default_points_in_flight(ctypes.byref(_band_shape(n, kl, ku)), int(npoints),
+                                                   ctypes.byref(out)), "psa_default_points_in_flight")
     return int(out.value)
 
 
@@ -105,8 +106,6 @@ class Workspace:
         self.offset = (-base) % 256
         self.ptr = base + self.offset
 
-    def fits(self, n: int, kl: int, ku: int, points: int, opts: Optional[LanczosOpts]) -> bool:
-        return workspace_bytes(n, kl, ku, min(points, 32), opts) <= self.nbytes
 
 
 def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), idx=None,
@@ -132,7 +131,7 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
             raise TypeError("idx must be a contiguous CUDA int32 tensor")
     o = opts or LanczosOpts()
     if workspace is None:
-        pif = points_in_flight or default_points_in_flight(max(npts, 1))
+        pif = points_in_flight or default_points_in_flight(n, kl, ku, max(npts, 1))
         workspace = Workspace(n, kl, ku, pif, o, device=dev)
     elif points_in_flight is not None:
         raise ValueError("pass either workspace or points_in_flight")

@@ -78,7 +78,7 @@ def load(path: str | None = None):
         lib.psa_workspace_bytes.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaLanczosOpts), i64,
                                             ctypes.POINTER(ctypes.c_size_t)]
         lib.psa_default_points_in_flight.restype = ctypes.c_int
-        lib.psa_default_points_in_flight.argtypes = [i64, ctypes.POINTER(i64)]
+        lib.psa_default_points_in_flight.argtypes = [ctypes.POINTER(PsaBand), i64, ctypes.POINTER(i64)]
         lib.psa_sigma_min.restype = ctypes.c_int
         lib.psa_sigma_min.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaGrid),
                                       ctypes.POINTER(dbl), i32, vp, i64, vp, vp, vp, vp,

@@ -15,25 +15,26 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Workspace: [flags: 256 B][q1: n complex][per-warp blocks]. A warp block holds
+// n row records of row_bytes, then alpha_k and beta_k^2 for k_max steps (see the
+// kernel's header comment).
 struct Layout {
-    size_t flags, q1, F, piv, Va, Vb, Vx, Ta, Tb, total;
+    size_t flags, q1, wdata, total;
+    int64_t warp_bytes;
+    int row_bytes;
 };
 
-// Byte offsets of the workspace arrays for P slots (see KParams).
-Layout layout(int64_t n, int kl, int ku, int kmax, int64_t P)
+int row_bytes_of(int kl, int ku) { return (2 * kl + ku + 1 + 3) * 512 + 128; }
+
+Layout layout(int64_t n, int kl, int ku, int kmax, int64_t nwarps)
 {
-    const int64_t S = 2 * kl + ku + 1;
     Layout L{};
+    L.row_bytes = row_bytes_of(kl, ku);
+    L.warp_bytes = (int64_t)align_up((size_t)n * L.row_bytes + 2 * (size_t)kmax * 32 * sizeof(double));
     size_t off = 0;
     L.flags = off; off += kAlign;
-    L.q1 = off;  off += align_up(sizeof(double2) * (size_t)n);
-    L.F = off;   off += align_up(sizeof(double2) * (size_t)n * S * P);
-    L.piv = off; off += align_up((size_t)n * P);
-    L.Va = off;  off += align_up(sizeof(double2) * (size_t)n * P);
-    L.Vb = off;  off += align_up(sizeof(double2) * (size_t)n * P);
-    L.Vx = off;  off += align_up(sizeof(double2) * (size_t)n * P);
-    L.Ta = off;  off += align_up(sizeof(double) * (size_t)kmax * P);
-    L.Tb = off;  off += align_up(sizeof(double) * (size_t)kmax * P);
+    L.q1 = off;    off += align_up(sizeof(double2) * (size_t)n);
+    L.wdata = off; off += (size_t)nwarps * L.warp_bytes;
     L.total = off;
     return L;
 }
@@ -41,6 +42,12 @@ Layout layout(int64_t n, int kl, int ku, int kmax, int64_t P)
 bool band_ok(const psa_band *A)
 {
     return A && A->n >= 1 && A->kl >= 0 && A->ku >= 0 && A->kl <= A->n - 1 && A->ku <= A->n - 1;
+}
+
+// Row offsets inside a warp block are 32-bit.
+bool fits_row_offsets(const psa_band *A)
+{
+    return (int64_t)A->n * row_bytes_of(A->kl, A->ku) < 2147483647LL;
 }
 
 bool opts_ok(const psa_lanczos_opts &o)
@@ -126,16 +133,27 @@ __global__ void k_probe_dfma(int iters, double m, double c)
     if (s == 1.2345678e-300) g_probe_sink = s;  // keeps the chains live
 }
 
-launch_fn pick_launcher(int kl, int ku)
+KernelOps pick_ops(int kl, int ku)
 {
     switch (kl) {
-    case 0: return launcher_kl0(ku);
-    case 1: return launcher_kl1(ku);
-    case 2: return launcher_kl2(ku);
-    case 3: return launcher_kl3(ku);
-    case 4: return launcher_kl4(ku);
-    default: return nullptr;
+    case 0: return kernel_ops_kl0(ku);
+    case 1: return kernel_ops_kl1(ku);
+    case 2: return kernel_ops_kl2(ku);
+    case 3: return kernel_ops_kl3(ku);
+    case 4: return kernel_ops_kl4(ku);
+    default: return KernelOps{nullptr, nullptr};
     }
+}
+
+// Threads that fill the device once with the kernel for (kl, ku).
+int full_threads(const KernelOps &ops, int64_t *out)
+{
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSA_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PSA_ECUDA;
+    if (ops.blocks_per_sm(&nb) != cudaSuccess || nb < 1) return PSA_ECUDA;
+    *out = (int64_t)sms * nb * kThreads;
+    return PSA_OK;
 }
 
 }  // namespace
@@ -175,18 +193,20 @@ int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts, int64_t
     if (!band_ok(A) || points_in_flight < 1 || !bytes) return PSA_EINVAL;
     const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
     if (!opts_ok(o)) return PSA_EINVAL;
-    const int64_t P = (points_in_flight + 31) / 32 * 32;
-    *bytes = layout(A->n, A->kl, A->ku, o.k_max, P).total;
+    const int64_t nwarps = (points_in_flight + 31) / 32;
+    *bytes = layout(A->n, A->kl, A->ku, o.k_max, nwarps).total;
     return PSA_OK;
 }
 
-int psa_default_points_in_flight(int64_t npoints, int64_t *out)
+int psa_default_points_in_flight(const psa_band *A, int64_t npoints, int64_t *out)
 {
-    if (npoints < 1 || !out) return PSA_EINVAL;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PSA_ECUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PSA_ECUDA;
-    const int64_t full = (int64_t)sms * 8 * 32;
+    if (!band_ok(A) || npoints < 1 || !out) return PSA_EINVAL;
+    if (A->kl > kMaxKL || A->ku > kMaxKU) return PSA_EUNSUPPORTED;
+    const KernelOps ops = pick_ops(A->kl, A->ku);
+    if (!ops.launch) return PSA_EUNSUPPORTED;
+    int64_t full = 0;
+    const int rc = full_threads(ops, &full);
+    if (rc != PSA_OK) return rc;
     const int64_t need = (npoints + 31) / 32 * 32;
     *out = need < full ? need : full;
     return PSA_OK;
@@ -209,31 +229,27 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     if (n_idx < 0 || (n_idx > 0 && !idx)) return PSA_EINVAL;
     const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
     if (!opts_ok(o)) return PSA_EINVAL;
-    if (A->kl > kMaxKL || A->ku > kMaxKU) return PSA_EUNSUPPORTED;
-    const launch_fn launch = pick_launcher(A->kl, A->ku);
-    if (!launch) return PSA_EUNSUPPORTED;
+    if (A->kl > kMaxKL || A->ku > kMaxKU || !fits_row_offsets(A)) return PSA_EUNSUPPORTED;
+    const KernelOps ops = pick_ops(A->kl, A->ku);
+    if (!ops.launch) return PSA_EUNSUPPORTED;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PSA_EWORKSPACE;
 
     const int64_t npts = idx ? n_idx : ngrid;
-    // points in flight: as many slots as the workspace holds, a multiple of 32,
-    // at most 16 warps per SM and no more than the points to evaluate
     const int64_t n = A->n;
-    const int S = 2 * A->kl + A->ku + 1;
-    const size_t per_slot = sizeof(double2) * (size_t)n * S + (size_t)n + 3 * sizeof(double2) * (size_t)n +
-                            2 * sizeof(double) * (size_t)o.k_max;
-    if (layout(n, A->kl, A->ku, o.k_max, 32).total > ws_bytes) return PSA_EWORKSPACE;
-    int64_t P = round_down((int64_t)(ws_bytes / per_slot), 32);  // upper bound: layout >= P * per_slot
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PSA_ECUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PSA_ECUDA;
-    const int64_t cap = (int64_t)sms * 16 * 32;
-    if (P > cap) P = cap;
-    const int64_t need = (npts + 31) / 32 * 32;
-    if (P > need) P = need < 32 ? 32 : need;
-    if (P >= 128) P = round_down(P, 128);
-    while (P > 32 && layout(n, A->kl, A->ku, o.k_max, P).total > ws_bytes) P -= 32;
-    if (P < 32) P = 32;  // layout(32) fits (checked above)
-    const Layout L = layout(n, A->kl, A->ku, o.k_max, P);
+    // points in flight: whole warps, as many as the workspace holds, at most one
+    // full occupancy of the device and no more than the points to evaluate
+    const Layout L1 = layout(n, A->kl, A->ku, o.k_max, 1);
+    if (L1.total > ws_bytes) return PSA_EWORKSPACE;
+    int64_t nwarps = (int64_t)((ws_bytes - (L1.total - (size_t)L1.warp_bytes)) / (size_t)L1.warp_bytes);
+    int64_t full = 0;
+    const int frc = full_threads(ops, &full);
+    if (frc != PSA_OK) return frc;
+    if (nwarps > full / 32) nwarps = full / 32;
+    const int64_t need_w = (npts + 31) / 32;
+    if (nwarps > need_w) nwarps = need_w < 1 ? 1 : need_w;
+    if (nwarps >= 4) nwarps = round_down(nwarps, 4);
+    const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps);
+    const int64_t P = nwarps * 32;
 
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
     char *ws = static_cast<char *>(workspace);
@@ -261,14 +277,11 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.status = status;
     p.steps = steps;
     p.flags = reinterpret_cast<const int *>(ws + L.flags);
+    p.counter = reinterpret_cast<int *>(ws + L.flags) + 1;
     p.q1 = reinterpret_cast<const double2 *>(ws + L.q1);
-    p.F = reinterpret_cast<double2 *>(ws + L.F);
-    p.piv = reinterpret_cast<uint8_t *>(ws + L.piv);
-    p.Va = reinterpret_cast<double2 *>(ws + L.Va);
-    p.Vb = reinterpret_cast<double2 *>(ws + L.Vb);
-    p.Vx = reinterpret_cast<double2 *>(ws + L.Vx);
-    p.Ta = reinterpret_cast<double *>(ws + L.Ta);
-    p.Tb = reinterpret_cast<double *>(ws + L.Tb);
+    p.wdata = ws + L.wdata;
+    p.warp_bytes = L.warp_bytes;
+    p.row_bytes = L.row_bytes;
     p.P = P;
 
     if (mask && n_eps == 0) {
@@ -290,7 +303,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
         if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
     }
     if (npts == 0) return PSA_OK;
-    if (launch(p, stream) != cudaSuccess) return PSA_ECUDA;
+    if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
     return PSA_OK;
 }
 

@@ -2,5 +2,5 @@
 #include "psa_kernel.cuh"
 
 namespace psa {
-launch_fn launcher_kl2(int ku) { return launcher_for_ku<2>(ku); }
+KernelOps kernel_ops_kl2(int ku) { return kernel_ops_for_ku<2>(ku); }
 }  // namespace psa

@@ -33,24 +33,26 @@ struct KParams {
     uint32_t *mask;
     int8_t *status;
     int32_t *steps;
-    // workspace: per slot t in [0, P), every array is [row][P] (row-major in row,
-    // slot fastest) so that a warp touches 32 consecutive slots per access
+    // workspace
     const int *flags;   // flags[0] != 0: a band entry of A is not finite
-    const double2 *q1;  // start vector, n values (shared by all slots)
-    double2 *F;         // factor rows: [n][S][P], S = 2kl + ku + 1
-    uint8_t *piv;       // pivot offsets: [n][P]
-    double2 *Va, *Vb, *Vx;  // Lanczos vectors: [n][P] each
-    double *Ta, *Tb;    // alpha_k, beta_k^2: [k_max][P] each
-    int64_t P;
+    int *counter;       // next group of 32 points (zeroed before the launch)
+    const double2 *q1;  // start vector, n values (shared by all warps)
+    char *wdata;        // per-warp blocks of warp_bytes, row records of row_bytes
+    int64_t warp_bytes;
+    int row_bytes;
+    int64_t P;          // threads launched (a multiple of kThreads)
 };
 
-using launch_fn = cudaError_t (*)(const KParams &, cudaStream_t);
+struct KernelOps {
+    cudaError_t (*launch)(const KParams &, cudaStream_t);
+    cudaError_t (*blocks_per_sm)(int *);  // resident blocks of kThreads per SM
+};
 
-// One launcher per compiled (kl, ku); defined in psa_inst_kl*.cu.
-launch_fn launcher_kl0(int ku);
-launch_fn launcher_kl1(int ku);
-launch_fn launcher_kl2(int ku);
-launch_fn launcher_kl3(int ku);
-launch_fn launcher_kl4(int ku);
+// One entry per compiled (kl, ku); defined in psa_inst_kl*.cu.
+KernelOps kernel_ops_kl0(int ku);
+KernelOps kernel_ops_kl1(int ku);
+KernelOps kernel_ops_kl2(int ku);
+KernelOps kernel_ops_kl3(int ku);
+KernelOps kernel_ops_kl4(int ku);
 
 }  // namespace psa

@@ -32,8 +32,9 @@
 //      status UNDERFLOW and sigma = 0.
 //   4. Mask bit l = (sigma <= eps_l) (paper Sec. 2.1, Eq. (sensitive_zone)).
 //
-// Workspace per slot (one slot per thread): every array is [row][P] so that a
-// warp's 32 accesses to one row are 32 consecutive 16-byte values.
+// Work distribution: each warp takes groups of 32 consecutive points from an
+// atomic counter until the points run out, so warps that meet fast-converging
+// points take more of them. Each warp owns one contiguous workspace block.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -190,28 +191,55 @@ __device__ __forceinline__ double ritz_top(const double *Ta, const double *Tb, i
 }
 
 // ------------------------------------------------------------------ kernel
+// Per-warp workspace block (one block per warp, the warp's 32 lanes interleaved
+// in 16-byte units so that every access of a warp is 512 contiguous bytes):
+//   row record j (row_bytes apart):  field f at f * 512 for f = 0 .. S+2
+//       f = 0            1 / U_jj
+//       f = 1 .. KW      U_{j, j+f}
+//       f = KW+1 .. S-1  multipliers l_{j+r, j}, r = 1 .. KL
+//       f = S, S+1, S+2  Lanczos vectors Va (q), Vb (u / w), Vx (solve work)
+//     then 32 pivot offsets (bytes)
+//   after n rows: alpha_k [k_max][32] and beta_k^2 [k_max][32] doubles.
 template <int KL, int KU>
-__global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
-{
-    constexpr int KW = KL + KU;        // superdiagonals of U after fill-in
-    constexpr int S = 2 * KL + KU + 1; // factor values per row: 1/U_jj, U_{j,j+1..j+KW}, l_{j+1..j+KL}
-    const int64_t P = p.P;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = p.n;
-    const int64_t ngrid = (int64_t)p.nx * p.ny;
+struct Shape {
+    static constexpr int KW = KL + KU;         // superdiagonals of U after fill-in
+    static constexpr int S = 2 * KL + KU + 1;  // factor values per row
+    static constexpr int FA = S, FB = S + 1, FX = S + 2;
+    static constexpr int PIV = (S + 3) * 512;
+    // 12 warps per SM while the elimination window is small, else 8
+    static constexpr int MIN_BLOCKS = ((KL + 1) * (KW + 1) <= 24) ? 3 : 2;
+};
 
-    double2 *const F = p.F + t;
-    uint8_t *const piv = p.piv + t;
-    double2 *const Va = p.Va + t;   // q_{k-1} -> q_k
-    double2 *const Vb = p.Vb + t;   // u_k (= beta_{k-1} q_k) -> w_k
-    double2 *const Vx = p.Vx + t;   // solve work vector
-    double *const Ta = p.Ta + t;
-    double *const Tb = p.Tb + t;
-    const int64_t SP = (int64_t)S * P;
+template <int KL, int KU>
+__global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_min(const KParams p)
+{
+    using SH = Shape<KL, KU>;
+    constexpr int KW = SH::KW;
+    constexpr int FA = SH::FA, FB = SH::FB, FX = SH::FX;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n = p.n;
+    const int RB = p.row_bytes;
+    const int64_t ngrid = (int64_t)p.nx * p.ny;
+    char *const wbase = p.wdata + warp * p.warp_bytes;
+    char *const rows = wbase + lane * 16;
+    uint8_t *const pivs = reinterpret_cast<uint8_t *>(wbase) + SH::PIV + lane;
+    double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)n * RB) + lane;
+    double *const Tb = Ta + (int64_t)p.k_max * 32;
+    constexpr int64_t TS = 32;  // stride of Ta / Tb in doubles
     const bool bad_input = p.flags[0] != 0;
 
-    for (int64_t base = 0; base < p.npts; base += P) {
-        const int64_t pt = base + t;
+#define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
+#define PIVOF(j) (pivs[(j) * RB])
+
+    for (;;) {
+        // the warp takes the next group of 32 points
+        int grp = 0;
+        if (lane == 0) grp = atomicAdd(p.counter, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        const int64_t first_pt = (int64_t)grp * 32;
+        if (first_pt >= p.npts) break;
+        const int64_t pt = first_pt + lane;
         int64_t flat = -1;
         if (pt < p.npts) {
             flat = p.idx ? (int64_t)p.idx[pt] : pt;
@@ -258,15 +286,14 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                 }
                 if (best == 0ULL) { singular = true; break; }
                 const double2 rp = c_rcp(W[0][0]);
-                double2 *const Fj = F + (int64_t)j * SP;
-                Fj[0] = rp;
+                FLD(j, 0) = rp;
 #pragma unroll
-                for (int c = 1; c <= KW; ++c) Fj[(int64_t)c * P] = W[0][c];
-                if (KL > 0) piv[(int64_t)j * P] = (uint8_t)pr;
+                for (int c = 1; c <= KW; ++c) FLD(j, c) = W[0][c];
+                if (KL > 0) PIVOF(j) = (uint8_t)pr;
 #pragma unroll
                 for (int r = 1; r <= KL; ++r) {
                     const double2 l = c_mul(W[r][0], rp);
-                    Fj[(int64_t)(KW + r) * P] = l;
+                    FLD(j, KW + r) = l;
 #pragma unroll
                     for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
                 }
@@ -276,8 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                     for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
                     W[r][KW] = make_double2(0.0, 0.0);
                 }
-                // next row i = j + 1 + KL, columns j+1 .. j+1+KW: d = c - KL
-                const int i = j + 1 + KL;
+                const int i = j + 1 + KL;  // next row, columns j+1 .. j+1+KW (d = c - KL)
 #pragma unroll
                 for (int c = 0; c <= KW; ++c) {
                     const int col = j + 1 + c;
@@ -308,43 +334,59 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                     double b2 = 0.0;
                     {
                         double2 X[KL + 1];
-                        auto make_u = [&](int ii) -> double2 {
-                            double2 u;
-                            if (first) {
-                                u = __ldg(&p.q1[ii]);
-                            } else {
-                                const double2 w = Vb[(int64_t)ii * P];
-                                const double2 q = Va[(int64_t)ii * P];
-                                u = make_double2(fma(-alpha, q.x, w.x), fma(-alpha, q.y, w.y));
-                            }
+                        auto make_u = [&](int ii, double2 w, double2 q) -> double2 {
+                            const double2 u = first ? w : make_double2(fma(-alpha, q.x, w.x), fma(-alpha, q.y, w.y));
                             b2 = fma(u.x, u.x, fma(u.y, u.y, b2));
-                            Vb[(int64_t)ii * P] = u;
+                            FLD(ii, FB) = u;
                             return u;
                         };
+                        auto load_w = [&](int ii, double2 &w, double2 &q) {
+                            if (first) { w = __ldg(&p.q1[ii]); q = make_double2(0.0, 0.0); }
+                            else { w = FLD(ii, FB); q = FLD(ii, FA); }
+                        };
 #pragma unroll
-                        for (int r = 0; r < KL; ++r) X[r] = (r < n) ? make_u(r) : make_double2(0.0, 0.0);
-                        for (int j = 0; j < n; ++j) {
-                            X[KL] = (j + KL < n) ? make_u(j + KL) : make_double2(0.0, 0.0);
+                        for (int r = 0; r < KL; ++r) {
+                            X[r] = make_double2(0.0, 0.0);
+                            if (r < n) { double2 w, q; load_w(r, w, q); X[r] = make_u(r, w, q); }
+                        }
+                        // row j needs pivot j, multipliers of column j and u_{j+KL}; prefetch row j+1
+                        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nq = make_double2(0.0, 0.0);
+                        int npv = 0;
+                        auto load_a = [&](int j) {
                             if (KL > 0) {
-                                const int pj = piv[(int64_t)j * P];
-                                const double2 *Fj = F + (int64_t)j * SP;
+                                npv = PIVOF(j);
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
+                            }
+                            if (j + KL < n) load_w(j + KL, nw, nq);
+                        };
+                        load_a(0);
+                        for (int j = 0; j < n; ++j) {
+                            double2 cl[KL + 1];
+#pragma unroll
+                            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
+                            const int cpv = npv;
+                            const double2 cw = nw, cq = nq;
+                            if (j + 1 < n) load_a(j + 1);
+                            X[KL] = (j + KL < n) ? make_u(j + KL, cw, cq) : make_double2(0.0, 0.0);
+                            if (KL > 0) {
 #pragma unroll
                                 for (int r = 1; r <= KL; ++r) {
-                                    const bool s = (pj == r);
+                                    const bool s = (cpv == r);
                                     const double2 a = X[0], b = X[r];
                                     X[0] = s ? b : a;
                                     X[r] = s ? a : b;
                                 }
 #pragma unroll
-                                for (int r = 1; r <= KL; ++r) X[r] = c_sub_mul(X[r], Fj[(int64_t)(KW + r) * P], X[0]);
+                                for (int r = 1; r <= KL; ++r) X[r] = c_sub_mul(X[r], cl[r], X[0]);
                             }
-                            Vx[(int64_t)j * P] = X[0];
+                            FLD(j, FX) = X[0];
 #pragma unroll
                             for (int r = 0; r < KL; ++r) X[r] = X[r + 1];
                         }
                     }
                     if (!first) {
-                        Tb[(int64_t)(k - 2) * P] = b2;  // beta_{k-1}^2 completes T_{k-1}
+                        Tb[(int64_t)(k - 2) * TS] = b2;  // beta_{k-1}^2 completes T_{k-1}
                         if (b2 == 0.0) { status = 0; break; }  // Krylov space exhausted: theta exact
                     }
                     if (!(b2 <= 1.7e308)) { status = 5; break; }  // overflow: sigma below range
@@ -357,14 +399,24 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                         double2 Y[KW + 1];
 #pragma unroll
                         for (int c = 0; c <= KW; ++c) Y[c] = make_double2(0.0, 0.0);
-                        for (int j = n - 1; j >= 0; --j) {
-                            const double2 *Fj = F + (int64_t)j * SP;
-                            double2 acc = Vx[(int64_t)j * P];
+                        double2 nu[KW + 1], nv;
+                        auto load_b = [&](int j) {
 #pragma unroll
-                            for (int c = 1; c <= KW; ++c) acc = c_sub_mul(acc, Fj[(int64_t)c * P], Y[c]);
-                            const double2 x = c_mul(acc, Fj[0]);
+                            for (int c = 0; c <= KW; ++c) nu[c] = FLD(j, c);
+                            nv = FLD(j, FX);
+                        };
+                        load_b(n - 1);
+                        for (int j = n - 1; j >= 0; --j) {
+                            double2 cu[KW + 1];
+#pragma unroll
+                            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
+                            double2 acc = nv;
+                            if (j > 0) load_b(j - 1);
+#pragma unroll
+                            for (int c = 1; c <= KW; ++c) acc = c_sub_mul(acc, cu[c], Y[c]);
+                            const double2 x = c_mul(acc, cu[0]);
                             emax = max(emax, max(exp_field(x.x), exp_field(x.y)));
-                            Vx[(int64_t)j * P] = x;
+                            FLD(j, FX) = x;
 #pragma unroll
                             for (int c = KW; c >= 2; --c) Y[c] = Y[c - 1];
                             if (KW >= 1) Y[1] = x;
@@ -381,18 +433,26 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
 #pragma unroll
                         for (int c = 0; c < KW; ++c) {
                             double2 v = make_double2(0.0, 0.0);
-                            if (c < n) { v = Vx[(int64_t)c * P]; v.x *= sc; v.y *= sc; }
+                            if (c < n) { v = FLD(c, FX); v.x *= sc; v.y *= sc; }
                             Acc[c] = v;
                         }
-                        for (int i = 0; i < n; ++i) {
-                            double2 v = make_double2(0.0, 0.0);
-                            if (i + KW < n) { v = Vx[(int64_t)(i + KW) * P]; v.x *= sc; v.y *= sc; }
-                            Acc[KW] = v;
-                            const double2 *Fi = F + (int64_t)i * SP;
-                            const double2 tt = c_mul_conj(Acc[0], Fi[0]);
-                            Vx[(int64_t)i * P] = tt;
+                        double2 nu[KW + 1], nv = make_double2(0.0, 0.0);
+                        auto load_d = [&](int i) {
 #pragma unroll
-                            for (int c = 1; c <= KW; ++c) Acc[c] = c_sub_conjmul(Acc[c], Fi[(int64_t)c * P], tt);
+                            for (int c = 0; c <= KW; ++c) nu[c] = FLD(i, c);
+                            nv = (i + KW < n) ? FLD(i + KW, FX) : make_double2(0.0, 0.0);
+                        };
+                        load_d(0);
+                        for (int i = 0; i < n; ++i) {
+                            double2 cu[KW + 1];
+#pragma unroll
+                            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
+                            Acc[KW] = make_double2(nv.x * sc, nv.y * sc);
+                            if (i + 1 < n) load_d(i + 1);
+                            const double2 tt = c_mul_conj(Acc[0], cu[0]);
+                            FLD(i, FX) = tt;
+#pragma unroll
+                            for (int c = 1; c <= KW; ++c) Acc[c] = c_sub_conjmul(Acc[c], cu[c], tt);
 #pragma unroll
                             for (int c = 0; c < KW; ++c) Acc[c] = Acc[c + 1];
                         }
@@ -403,58 +463,72 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                     const double f = (invb * pow2i(clampi(es - e1, -1022, 1023))) * pow2i(clampi(-e1, -1022, 1023));
                     double asum = 0.0;
                     {
-                        auto emit = [&](int ii, double2 y) {
-                            const double2 u = Vb[(int64_t)ii * P];
+                        auto emit = [&](int ii, double2 y, double2 u, double2 qp) {
                             const double2 q = make_double2(u.x * invb, u.y * invb);
-                            double2 w;
-                            if (first) {
-                                w = make_double2(f * y.x, f * y.y);
-                            } else {
-                                const double2 qp = Va[(int64_t)ii * P];
-                                w = make_double2(fma(f, y.x, -(beta * qp.x)), fma(f, y.y, -(beta * qp.y)));
-                            }
+                            const double2 w = first ? make_double2(f * y.x, f * y.y)
+                                                    : make_double2(fma(f, y.x, -(beta * qp.x)), fma(f, y.y, -(beta * qp.y)));
                             asum = fma(q.x, w.x, fma(q.y, w.y, asum));
-                            Va[(int64_t)ii * P] = q;
-                            Vb[(int64_t)ii * P] = w;
+                            FLD(ii, FA) = q;
+                            FLD(ii, FB) = w;
                         };
                         double2 T[KL + 1];
 #pragma unroll
                         for (int r = 0; r <= KL; ++r) T[r] = make_double2(0.0, 0.0);
+                        // row j needs t_j, multipliers of column j, pivot j and (u, q_prev) at j + KL
+                        double2 nl[KL + 1], nt, nu = make_double2(0.0, 0.0), nqp = make_double2(0.0, 0.0);
+                        int npv = 0;
+                        auto load_e = [&](int j) {
+                            nt = FLD(j, FX);
+                            if (KL > 0) {
+                                npv = PIVOF(j);
+#pragma unroll
+                                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
+                            }
+                            if (j + KL < n) {
+                                nu = FLD(j + KL, FB);
+                                nqp = first ? make_double2(0.0, 0.0) : FLD(j + KL, FA);
+                            }
+                        };
+                        load_e(n - 1);
                         for (int j = n - 1; j >= 0; --j) {
+                            double2 cl[KL + 1];
+#pragma unroll
+                            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
+                            const int cpv = npv;
+                            const double2 ct = nt, cu = nu, cqp = nqp;
+                            if (j > 0) load_e(j - 1);
 #pragma unroll
                             for (int r = KL; r >= 1; --r) T[r] = T[r - 1];
-                            T[0] = Vx[(int64_t)j * P];
+                            T[0] = ct;
                             if (KL > 0) {
-                                const double2 *Fj = F + (int64_t)j * SP;
 #pragma unroll
-                                for (int r = 1; r <= KL; ++r) T[0] = c_sub_conjmul(T[0], Fj[(int64_t)(KW + r) * P], T[r]);
-                                const int pj = piv[(int64_t)j * P];
+                                for (int r = 1; r <= KL; ++r) T[0] = c_sub_conjmul(T[0], cl[r], T[r]);
 #pragma unroll
                                 for (int r = 1; r <= KL; ++r) {
-                                    const bool s = (pj == r);
+                                    const bool s = (cpv == r);
                                     const double2 a = T[0], b = T[r];
                                     T[0] = s ? b : a;
                                     T[r] = s ? a : b;
                                 }
-                                if (j + KL < n) emit(j + KL, T[KL]);
+                                if (j + KL < n) emit(j + KL, T[KL], cu, cqp);
                             } else {
-                                emit(j, T[0]);
+                                emit(j, T[0], cu, cqp);
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < KL; ++r)
-                            if (r < n) emit(r, T[r]);
+                            if (r < n) emit(r, T[r], FLD(r, FB), first ? make_double2(0.0, 0.0) : FLD(r, FA));
                     }
                     alpha = asum;
-                    Ta[(int64_t)(k - 1) * P] = alpha;
+                    Ta[(int64_t)(k - 1) * TS] = alpha;
                     ksteps = k;
 
                     // ---------------- 3. Ritz value and stopping test
                     if (k >= kr0) {
                         double th;
                         if (k == 1) th = alpha;
-                        else if (kth == k - 1) th = ritz_top(Ta, Tb, P, k, theta, dprev, alpha, b2);
-                        else th = ritz_top_cold(Ta, Tb, P, k);
+                        else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, b2);
+                        else th = ritz_top_cold(Ta, Tb, TS, k);
                         const bool have_prev = (kth == k - 1);
                         theta_prev = theta;
                         theta = th;
@@ -465,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
                     if (k >= kmax) break;
                 }
                 if (status != 5 && kth != ksteps && ksteps >= 1) {
-                    theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, P, ksteps);
+                    theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, TS, ksteps);
                     kth = ksteps;
                 }
                 if (status != 5) {
@@ -491,34 +565,36 @@ __global__ void __launch_bounds__(kThreads) k_sigma_min(const KParams p)
             if (p.steps) p.steps[flat] = ksteps;
         }
     }
+#undef FLD
+#undef PIVOF
 }
 
 template <int KL, int KU>
 cudaError_t launch_sigma_min(const KParams &p, cudaStream_t stream)
 {
     const int threads = (p.P % kThreads == 0) ? kThreads : 32;
-    const unsigned blocks = (unsigned)(p.P / threads);
-    k_sigma_min<KL, KU><<<blocks, threads, 0, stream>>>(p);
+    k_sigma_min<KL, KU><<<(unsigned)(p.P / threads), threads, 0, stream>>>(p);
     return cudaGetLastError();
+}
+
+template <int KL, int KU>
+cudaError_t blocks_per_sm(int *nb)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_sigma_min<KL, KU>, kThreads, 0);
 }
 
 }  // namespace dev
 
-// Table of launchers for one kl and ku = 0 .. kMaxKU.
+// Launch and occupancy entry points for one kl and ku = 0 .. kMaxKU.
 template <int KL>
-launch_fn launcher_for_ku(int ku)
+KernelOps kernel_ops_for_ku(int ku)
 {
     switch (ku) {
-    case 0: return &dev::launch_sigma_min<KL, 0>;
-    case 1: return &dev::launch_sigma_min<KL, 1>;
-    case 2: return &dev::launch_sigma_min<KL, 2>;
-    case 3: return &dev::launch_sigma_min<KL, 3>;
-    case 4: return &dev::launch_sigma_min<KL, 4>;
-    case 5: return &dev::launch_sigma_min<KL, 5>;
-    case 6: return &dev::launch_sigma_min<KL, 6>;
-    case 7: return &dev::launch_sigma_min<KL, 7>;
-    case 8: return &dev::launch_sigma_min<KL, 8>;
-    default: return nullptr;
+#define PSA_KU_CASE(K) case K: return KernelOps{&dev::launch_sigma_min<KL, K>, &dev::blocks_per_sm<KL, K>};
+    PSA_KU_CASE(0) PSA_KU_CASE(1) PSA_KU_CASE(2) PSA_KU_CASE(3) PSA_KU_CASE(4)
+    PSA_KU_CASE(5) PSA_KU_CASE(6) PSA_KU_CASE(7) PSA_KU_CASE(8)
+#undef PSA_KU_CASE
+    default: return KernelOps{nullptr, nullptr};
     }
 }
 
