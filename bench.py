@@ -264,9 +264,14 @@ def run_gpu(args):
     flops = algorithmic_flops(steps, n, kl, ku)
     mean_ms = dev_ms / args.steps if ws_ == 1 else float(np.mean(step_ms))
     achieved = flops / (mean_ms * 1e-3) / 1e12
-    # lanes idle inside a warp: steps of 32 consecutive points vs the warp's maximum
-    sw = steps[: steps.size // 32 * 32].reshape(-1, 32)
-    lane_util = float(sw.sum() / (sw.max(axis=1).sum() * 32))
+    # lanes busy inside a warp: a warp holds an 8 x 4 tile of the grid and runs
+    # until its slowest point stops
+    k2 = steps.reshape(grid.ny, grid.nx)
+    ty, tx = -(-grid.ny // 4), -(-grid.nx // 8)
+    kp = np.zeros((ty * 4, tx * 8), dtype=np.int64)
+    kp[:grid.ny, :grid.nx] = k2
+    tiles = kp.reshape(ty, 4, tx, 8).transpose(0, 2, 1, 3).reshape(-1, 32)
+    lane_util = float(tiles.sum() / (tiles.max(axis=1).sum() * 32))
 
     if args.case != "mid":
         if rank == 0:
@@ -297,7 +302,7 @@ def run_gpu(args):
     lvl = EPS.index(EPS_RESTRICT)
     s_true = ((mask >> lvl) & 1).astype(bool)
     region = dilate(s_true, 5)
-    idx = torch.as_tensor(np.flatnonzero(region.ravel()).astype(np.int32), device=dev)
+    idx = torch.as_tensor(psa.tile_order(np.flatnonzero(region.ravel()), grid.nx), device=dev)
     psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, idx=idx, opts=opts, workspace=wsp)
     torch.cuda.synchronize(dev)
     r_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

@@ -26,7 +26,7 @@ from .inputs import Grid
 
 __all__ = [
     "Grid", "LanczosOpts", "SigmaMinResult", "Workspace", "sigma_min", "workspace_bytes",
-    "default_points_in_flight", "probe_dfma_rate", "library_path", "PsaError",
+    "default_points_in_flight", "probe_dfma_rate", "library_path", "PsaError", "tile_order",
     "PT_OK", "PT_SINGULAR", "PT_NOT_CONVERGED", "PT_NONFINITE", "PT_NOT_EVALUATED", "PT_UNDERFLOW",
 ]
 
@@ -154,6 +154,20 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
                            s.cuda_stream)
     _native.check(rc, "psa_sigma_min")
     return out
+
+
+def tile_order(flat_idx, nx: int):
+    """Flat grid indices reordered into 8 x 4 tiles (the full-grid work order).
+
+    Restricted mode hands the list to warps in chunks of 32 entries; in this
+    order a chunk covers a compact patch of the grid whose points take similar
+    Lanczos step counts. Returns an int32 numpy array.
+    """
+    import numpy as np
+    f = np.asarray(flat_idx, dtype=np.int64).ravel()
+    i, j = f // nx, f % nx
+    key = ((i // 4) * ((nx + 7) // 8) + (j // 8)) * 32 + (i % 4) * 8 + (j % 8)
+    return f[np.argsort(key, kind="stable")].astype(np.int32)
 
 
 def probe_dfma_rate(iters: int = 4096, stream=None) -> float:

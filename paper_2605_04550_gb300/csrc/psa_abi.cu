@@ -245,7 +245,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     const int frc = full_threads(ops, &full);
     if (frc != PSA_OK) return frc;
     if (nwarps > full / 32) nwarps = full / 32;
-    const int64_t need_w = (npts + 31) / 32;
+    const int64_t need_w = idx ? (npts + 31) / 32 : (int64_t)((g->nx + 7) / 8) * ((g->ny + 3) / 4);
     if (nwarps > need_w) nwarps = need_w < 1 ? 1 : need_w;
     if (nwarps >= 4) nwarps = round_down(nwarps, 4);
     const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps);
@@ -267,6 +267,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.ny = g->ny;
     p.idx = idx;
     p.npts = npts;
+    p.ngroups = idx ? (npts + 31) / 32 : (int64_t)((g->nx + 7) / 8) * ((g->ny + 3) / 4);
     for (int l = 0; l < kMaxEps; ++l) p.eps[l] = l < n_eps ? eps[l] : 0.0;
     p.n_eps = n_eps;
     p.k_min = o.k_min;

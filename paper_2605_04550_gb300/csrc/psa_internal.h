@@ -22,6 +22,7 @@ struct KParams {
     // points: idx == nullptr -> flat index = point number; else idx[point]
     const int32_t *idx;
     int64_t npts;
+    int64_t ngroups;  // groups of 32 points: 8 x 4 grid tiles (full grid) or list chunks
     // epsilon levels
     double eps[kMaxEps];
     int n_eps;

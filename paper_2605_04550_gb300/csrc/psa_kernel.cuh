@@ -32,9 +32,12 @@
 //      status UNDERFLOW and sigma = 0.
 //   4. Mask bit l = (sigma <= eps_l) (paper Sec. 2.1, Eq. (sensitive_zone)).
 //
-// Work distribution: each warp takes groups of 32 consecutive points from an
-// atomic counter until the points run out, so warps that meet fast-converging
-// points take more of them. Each warp owns one contiguous workspace block.
+// Work distribution: each warp takes groups of 32 points from an atomic
+// counter until the points run out, so warps that meet fast-converging points
+// take more of them. On the full grid a group is an 8 x 4 tile of the grid
+// (neighbouring points converge in similar step counts, so fewer lanes idle
+// than with 32 points of one grid row); in restricted mode it is 32
+// consecutive entries of the list. Each warp owns one contiguous workspace block.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -228,6 +231,9 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
     double *const Tb = Ta + (int64_t)p.k_max * 32;
     constexpr int64_t TS = 32;  // stride of Ta / Tb in doubles
     const bool bad_input = p.flags[0] != 0;
+    __shared__ double2 Aw_all[kThreads / 32][KW + 1][32];
+    double2 (*const Aw)[32] = Aw_all[threadIdx.x >> 5];
+    double zr = 0.0, zi = 0.0;
 
 #define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
 #define PIVOF(j) (pivs[(j) * RB])
@@ -237,85 +243,116 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
         int grp = 0;
         if (lane == 0) grp = atomicAdd(p.counter, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
-        const int64_t first_pt = (int64_t)grp * 32;
-        if (first_pt >= p.npts) break;
-        const int64_t pt = first_pt + lane;
+        if (grp >= p.ngroups) break;
         int64_t flat = -1;
-        if (pt < p.npts) {
-            flat = p.idx ? (int64_t)p.idx[pt] : pt;
-            if (flat >= ngrid) flat = -1;
+        if (p.idx) {
+            // restricted mode: 32 consecutive entries of the list
+            const int64_t pt = (int64_t)grp * 32 + lane;
+            if (pt < p.npts) {
+                flat = (int64_t)p.idx[pt];
+                if (flat >= ngrid) flat = -1;
+            }
+        } else {
+            // full grid: an 8 x 4 tile (8 abscissae, 4 ordinates); neighbouring points
+            // take similar Lanczos step counts, so the warp's lanes stay busy together
+            const int tiles_x = (p.nx + 7) >> 3;
+            const int ty = (int)(grp / tiles_x), tx = (int)(grp - (int64_t)ty * tiles_x);
+            const int i = ty * 4 + (lane >> 3), j = tx * 8 + (lane & 7);
+            if (i < p.ny && j < p.nx) flat = (int64_t)i * p.nx + j;
         }
-        if (flat >= 0) {
-            const int gi = (int)(flat / p.nx);
-            const int gj = (int)(flat - (int64_t)gi * p.nx);
-            const double zr = fma((double)gj, p.hx, p.re_min);
-            const double zi = fma((double)gi, p.hy, p.im_min);
+        // every lane runs the factorisation (lanes without a point on a dummy z), so
+        // that the warp can stage the bands of A cooperatively
+        const bool have = flat >= 0;
+        {
+            const int gi = have ? (int)(flat / p.nx) : 0;
+            const int gj = have ? (int)(flat - (int64_t)gi * p.nx) : 0;
+            zr = fma((double)gj, p.hx, p.re_min);
+            zi = fma((double)gi, p.hy, p.im_min);
+        }
 
-            // ---------------- 1. banded LU with partial pivoting
-            double2 W[KL + 1][KW + 1];
+        // ---------------- 1. banded LU with partial pivoting
+        // A's diagonals for rows R0 .. R0+31 sit in this warp's shared-memory window,
+        // loaded with one coalesced 512-byte access per diagonal:
+        //   Aw[c][r - R0] = A[r][r + c - KL] = bands[c * n + r],  c = 0 .. KW
+        int R0 = 0;
+        auto stage = [&](int r0) {
+            __syncwarp();
 #pragma unroll
-            for (int r = 0; r <= KL; ++r)
+            for (int c = 0; c <= KW; ++c) {
+                const int r = r0 + lane;
+                Aw[c][lane] = (r < n) ? __ldg(&p.bands[(int64_t)c * n + r]) : make_double2(0.0, 0.0);
+            }
+            __syncwarp();
+        };
+        if (!bad_input) stage(0);
+        double2 W[KL + 1][KW + 1];
+#pragma unroll
+        for (int r = 0; r <= KL; ++r)
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) {
+                const int d = c - r;
+                double2 v = make_double2(0.0, 0.0);
+                if (!bad_input && d >= -KL && d <= KU && r < n && c < n) {
+                    const double2 a = Aw[d + KL][r];
+                    v = (d == 0) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+                }
+                W[r][c] = v;
+            }
+        bool singular = false;
+        for (int j = 0; j < (bad_input ? 0 : n); ++j) {
+            int pr = 0;
+            unsigned long long best = abs_bits(fabs(W[0][0].x) + fabs(W[0][0].y));
+#pragma unroll
+            for (int r = 1; r <= KL; ++r) {
+                const unsigned long long v = abs_bits(fabs(W[r][0].x) + fabs(W[r][0].y));
+                if (v > best) { best = v; pr = r; }
+            }
+#pragma unroll
+            for (int r = 1; r <= KL; ++r) {
+                const bool s = (pr == r);
 #pragma unroll
                 for (int c = 0; c <= KW; ++c) {
-                    const int d = c - r;
-                    double2 v = make_double2(0.0, 0.0);
-                    if (d >= -KL && d <= KU && r < n && c < n) {
-                        const double2 a = __ldg(&p.bands[(int64_t)(d + KL) * n + r]);
-                        v = (d == 0) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
-                    }
-                    W[r][c] = v;
-                }
-            bool singular = false;
-            for (int j = 0; j < (bad_input ? 0 : n); ++j) {
-                int pr = 0;
-                unsigned long long best = abs_bits(fabs(W[0][0].x) + fabs(W[0][0].y));
-#pragma unroll
-                for (int r = 1; r <= KL; ++r) {
-                    const unsigned long long v = abs_bits(fabs(W[r][0].x) + fabs(W[r][0].y));
-                    if (v > best) { best = v; pr = r; }
-                }
-#pragma unroll
-                for (int r = 1; r <= KL; ++r) {
-                    const bool s = (pr == r);
-#pragma unroll
-                    for (int c = 0; c <= KW; ++c) {
-                        const double2 a = W[0][c], b = W[r][c];
-                        W[0][c] = s ? b : a;
-                        W[r][c] = s ? a : b;
-                    }
-                }
-                if (best == 0ULL) { singular = true; break; }
-                const double2 rp = c_rcp(W[0][0]);
-                FLD(j, 0) = rp;
-#pragma unroll
-                for (int c = 1; c <= KW; ++c) FLD(j, c) = W[0][c];
-                if (KL > 0) PIVOF(j) = (uint8_t)pr;
-#pragma unroll
-                for (int r = 1; r <= KL; ++r) {
-                    const double2 l = c_mul(W[r][0], rp);
-                    FLD(j, KW + r) = l;
-#pragma unroll
-                    for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
-                }
-#pragma unroll
-                for (int r = 0; r < KL; ++r) {
-#pragma unroll
-                    for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
-                    W[r][KW] = make_double2(0.0, 0.0);
-                }
-                const int i = j + 1 + KL;  // next row, columns j+1 .. j+1+KW (d = c - KL)
-#pragma unroll
-                for (int c = 0; c <= KW; ++c) {
-                    const int col = j + 1 + c;
-                    double2 v = make_double2(0.0, 0.0);
-                    if (i < n && col < n) {
-                        const double2 a = __ldg(&p.bands[(int64_t)c * n + i]);
-                        v = (c == KL) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
-                    }
-                    W[KL][c] = v;
+                    const double2 a = W[0][c], b = W[r][c];
+                    W[0][c] = s ? b : a;
+                    W[r][c] = s ? a : b;
                 }
             }
+            // an exact zero pivot column: B is singular; the lane keeps stepping with a
+            // unit pivot (its factor is not used) so that the warp stays together
+            if (best == 0ULL) { singular = true; W[0][0] = make_double2(1.0, 0.0); }
+            const double2 rp = c_rcp(W[0][0]);
+            FLD(j, 0) = rp;
+#pragma unroll
+            for (int c = 1; c <= KW; ++c) FLD(j, c) = W[0][c];
+            if (KL > 0) PIVOF(j) = (uint8_t)pr;
+#pragma unroll
+            for (int r = 1; r <= KL; ++r) {
+                const double2 l = c_mul(W[r][0], rp);
+                FLD(j, KW + r) = l;
+#pragma unroll
+                for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < KL; ++r) {
+#pragma unroll
+                for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
+                W[r][KW] = make_double2(0.0, 0.0);
+            }
+            const int i = j + 1 + KL;  // next row, columns j+1 .. j+1+KW (d = c - KL)
+            if (i - R0 >= 32) { R0 += 32; stage(R0); }
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) {
+                const int col = j + 1 + c;
+                double2 v = make_double2(0.0, 0.0);
+                if (i < n && col < n) {
+                    const double2 a = Aw[c][i - R0];
+                    v = (c == KL) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+                }
+                W[KL][c] = v;
+            }
+        }
 
+        if (have) {
             double sigma = 0.0;
             int status = bad_input ? 3 : 1;  // NONFINITE input, else SINGULAR
             int ksteps = 0;
