@@ -19,11 +19,13 @@
 //   1. B = zI - A is factored by Gaussian elimination with partial pivoting
 //      inside the band (pivot = largest |Re| + |Im| of rows j..j+kl, first on
 //      ties), with a (kl+1) x (kl+ku+1) register window sliding down the band.
-//   2. Lanczos on H' = (B B^*)^{-1} / 2^(2 e1): step k solves B x = u_k
-//      (interchanges + L forward, U backward), rescales x by a power of two,
-//      solves B^* y = x (U^* forward, L^* backward + interchanges), and forms
-//      w_k = H' q_k - beta_{k-1} q_{k-1}, alpha_k = Re <q_k, w_k>,
-//      u_{k+1} = w_k - alpha_k q_k, beta_k = |u_{k+1}|.
+//   2. Lanczos on H' = (B B^*)^{-1} / 2^(2 e1): step k solves B x = v_k
+//      (interchanges + L forward, U backward), solves B^* y = x (U^* forward,
+//      L^* backward + interchanges), and forms w_k (proportional to
+//      H' q_k - beta_{k-1} q_{k-1}), alpha_k = Re <q_k, H' q_k - ...>, and
+//      in the next step's first sweep v_{k+1} (proportional to
+//      u_{k+1} = w_k - alpha_k q_k) and beta_k = |u_{k+1}|. The stored vectors
+//      keep a fixed power-of-two scale, so no sweep normalises them.
 //   3. theta_k = lambda_max(T_k) by Newton's method on the characteristic
 //      polynomial of T_k from above (monotone, warm-started at the previous
 //      Ritz value); stop when theta_k - theta_{k-1} <= tol * theta_k, at
@@ -78,6 +80,13 @@ __device__ __forceinline__ int exp_field(double d) { return (__double2hiint(d) >
 // 2^e for e in [-1022, 1023], exact.
 __device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+// v * 2^e for |e| up to ~3000, as exact power-of-two products (barring over/underflow).
+__device__ __forceinline__ double scale2(double v, int e)
+{
+    while (e > 1000) { v *= pow2i(1000); e -= 1000; }
+    while (e < -1000) { v *= pow2i(-1000); e += 1000; }
+    return v * pow2i(e);
+}
 
 // 1 / a by Smith's scaled formula (R. L. Smith, "Algorithm 116: Complex
 // division", CACM 5(8), 1962): with |p| >= |q| the larger and smaller of
@@ -358,7 +367,15 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
             int ksteps = 0;
             if (!singular && !bad_input) {
                 // ---------------- 2. Lanczos on H'
-                double alpha = 0.0, theta = 0.0, theta_prev = 0.0, dprev = 0.0;
+                // The stored Lanczos vectors are v_k = u_k = beta_{k-1} q_k (v_1 = q_1), not
+                // normalised: 1/beta rides on the scalars of the next sweep. 2^e1 is the
+                // binary exponent of the largest component of B^{-1} q_1 (about 1/sigma);
+                // for |e1| <= 450 the solves of later steps stay inside the double range
+                // (x ~ beta 2^e1, y ~ beta 2^(2 e1) theta') and need no rescaling.
+                double theta = 0.0, theta_prev = 0.0, dprev = 0.0;
+                double acoef = 0.0;   // v_k = w_{k-1} - acoef * v_{k-1}
+                double beta_p = 0.0;  // beta_{k-1}
+                double beta_pp = 0.0; // beta_{k-2}
                 int e1 = 0;
                 int kth = 0;  // step whose Ritz value `theta` holds
                 const int kmax = p.k_max;
@@ -367,27 +384,29 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                 status = 2;  // NOT_CONVERGED
                 for (int k = 1;; ++k) {
                     const bool first = (k == 1);
-                    // (a) u_k = w_{k-1} - alpha_{k-1} q_{k-1} (q_1 at k = 1); |u_k|^2; L forward
+                    const int fcur = (k & 1) ? FA : FB;   // v_k and, after (e), ...
+                    const int fprv = (k & 1) ? FB : FA;   // v_{k-1}, replaced by w_k in (e)
+                    // (a) v_k = w_{k-1} - acoef v_{k-1} (q_1 at k = 1); |v_k|^2; interchanges + L forward
                     double b2 = 0.0;
                     {
                         double2 X[KL + 1];
-                        auto make_u = [&](int ii, double2 w, double2 q) -> double2 {
-                            const double2 u = first ? w : make_double2(fma(-alpha, q.x, w.x), fma(-alpha, q.y, w.y));
-                            b2 = fma(u.x, u.x, fma(u.y, u.y, b2));
-                            FLD(ii, FB) = u;
-                            return u;
+                        auto make_v = [&](int ii, double2 w, double2 vp) -> double2 {
+                            const double2 v = first ? w : make_double2(fma(-acoef, vp.x, w.x), fma(-acoef, vp.y, w.y));
+                            b2 = fma(v.x, v.x, fma(v.y, v.y, b2));
+                            FLD(ii, fcur) = v;
+                            return v;
                         };
-                        auto load_w = [&](int ii, double2 &w, double2 &q) {
-                            if (first) { w = __ldg(&p.q1[ii]); q = make_double2(0.0, 0.0); }
-                            else { w = FLD(ii, FB); q = FLD(ii, FA); }
+                        auto load_w = [&](int ii, double2 &w, double2 &vp) {
+                            if (first) { w = __ldg(&p.q1[ii]); vp = make_double2(0.0, 0.0); }
+                            else { w = FLD(ii, fcur); vp = FLD(ii, fprv); }
                         };
 #pragma unroll
                         for (int r = 0; r < KL; ++r) {
                             X[r] = make_double2(0.0, 0.0);
-                            if (r < n) { double2 w, q; load_w(r, w, q); X[r] = make_u(r, w, q); }
+                            if (r < n) { double2 w, vp; load_w(r, w, vp); X[r] = make_v(r, w, vp); }
                         }
-                        // row j needs pivot j, multipliers of column j and u_{j+KL}; prefetch row j+1
-                        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nq = make_double2(0.0, 0.0);
+                        // row j needs pivot j, multipliers of column j and v_{j+KL}; prefetch row j+1
+                        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
                         int npv = 0;
                         auto load_a = [&](int j) {
                             if (KL > 0) {
@@ -395,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 #pragma unroll
                                 for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
                             }
-                            if (j + KL < n) load_w(j + KL, nw, nq);
+                            if (j + KL < n) load_w(j + KL, nw, nvp);
                         };
                         load_a(0);
                         for (int j = 0; j < n; ++j) {
@@ -403,9 +422,9 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 #pragma unroll
                             for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
                             const int cpv = npv;
-                            const double2 cw = nw, cq = nq;
+                            const double2 cw = nw, cvp = nvp;
                             if (j + 1 < n) load_a(j + 1);
-                            X[KL] = (j + KL < n) ? make_u(j + KL, cw, cq) : make_double2(0.0, 0.0);
+                            X[KL] = (j + KL < n) ? make_v(j + KL, cw, cvp) : make_double2(0.0, 0.0);
                             if (KL > 0) {
 #pragma unroll
                                 for (int r = 1; r <= KL; ++r) {
@@ -422,13 +441,15 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                             for (int r = 0; r < KL; ++r) X[r] = X[r + 1];
                         }
                     }
+                    double invb = 1.0;
                     if (!first) {
-                        Tb[(int64_t)(k - 2) * TS] = b2;  // beta_{k-1}^2 completes T_{k-1}
                         if (b2 == 0.0) { status = 0; break; }  // Krylov space exhausted: theta exact
+                        if (!(b2 <= 1.7e308)) { status = 5; break; }  // overflow: sigma below range
+                        Tb[(int64_t)(k - 2) * TS] = b2;  // beta_{k-1}^2 = |v_k|^2 completes T_{k-1}
+                        beta_pp = beta_p;
+                        beta_p = sqrt(b2);
+                        invb = 1.0 / beta_p;
                     }
-                    if (!(b2 <= 1.7e308)) { status = 5; break; }  // overflow: sigma below range
-                    const double beta = sqrt(b2);
-                    const double invb = 1.0 / beta;
 
                     // (b) U x = Vx backward; x_j = (Vx_j - sum U_{j,j+c} x_{j+c}) / U_jj
                     int emax = 0;
@@ -460,7 +481,13 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                         }
                     }
                     if (emax >= 2047) { status = 5; break; }
-                    const int es = clampi(emax - 1023, -1000, 1000);
+                    // x is rescaled by 2^-es at the first step (fixing e1), at every step of
+                    // a point with |e1| > 450, and at any step whose y (about x 2^e1) could
+                    // come near the top of the double range. The decision is taken per warp;
+                    // an exact power-of-two scale leaves every lane's result unchanged.
+                    const bool scaled = __any_sync(__activemask(), first || e1 > 450 || e1 < -450 ||
+                                                                       (emax - 1023) + e1 + 24 > 1000);
+                    const int es = scaled ? clampi(emax - 1023, -1000, 1000) : 0;
                     if (first) e1 = es;
                     const double sc = pow2i(-es);
 
@@ -470,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 #pragma unroll
                         for (int c = 0; c < KW; ++c) {
                             double2 v = make_double2(0.0, 0.0);
-                            if (c < n) { v = FLD(c, FX); v.x *= sc; v.y *= sc; }
+                            if (c < n) { v = FLD(c, FX); if (scaled) { v.x *= sc; v.y *= sc; } }
                             Acc[c] = v;
                         }
                         double2 nu[KW + 1], nv = make_double2(0.0, 0.0);
@@ -484,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                             double2 cu[KW + 1];
 #pragma unroll
                             for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
-                            Acc[KW] = make_double2(nv.x * sc, nv.y * sc);
+                            Acc[KW] = scaled ? make_double2(nv.x * sc, nv.y * sc) : nv;
                             if (i + 1 < n) load_d(i + 1);
                             const double2 tt = c_mul_conj(Acc[0], cu[0]);
                             FLD(i, FX) = tt;
@@ -495,24 +522,24 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                         }
                     }
 
-                    // (e) L^* backward with interchanges; as each y_i becomes final:
-                    //     q_i = u_i / beta_{k-1}, w_i = f y_i - beta_{k-1} q_{k-1,i}, alpha += Re(conj(q_i) w_i)
-                    const double f = (invb * pow2i(clampi(es - e1, -1022, 1023))) * pow2i(clampi(-e1, -1022, 1023));
+                    // (e) L^* backward with interchanges; as each y_i becomes final,
+                    //     w_i = F y_i - G v_{k-1,i} (= (H' q_k - beta_{k-1} q_{k-1})_i)
+                    //     and asum += Re(conj(v_{k,i}) w_i)
+                    const double F = scale2(first ? 1.0 : invb, es - 2 * e1);
+                    const double G = (k == 2) ? beta_p : beta_p / (beta_pp > 0.0 ? beta_pp : 1.0);
                     double asum = 0.0;
                     {
-                        auto emit = [&](int ii, double2 y, double2 u, double2 qp) {
-                            const double2 q = make_double2(u.x * invb, u.y * invb);
-                            const double2 w = first ? make_double2(f * y.x, f * y.y)
-                                                    : make_double2(fma(f, y.x, -(beta * qp.x)), fma(f, y.y, -(beta * qp.y)));
-                            asum = fma(q.x, w.x, fma(q.y, w.y, asum));
-                            FLD(ii, FA) = q;
-                            FLD(ii, FB) = w;
+                        auto emit = [&](int ii, double2 y, double2 vc, double2 vp) {
+                            const double2 w = first ? make_double2(F * y.x, F * y.y)
+                                                    : make_double2(fma(F, y.x, -(G * vp.x)), fma(F, y.y, -(G * vp.y)));
+                            asum = fma(vc.x, w.x, fma(vc.y, w.y, asum));
+                            FLD(ii, fprv) = w;
                         };
                         double2 T[KL + 1];
 #pragma unroll
                         for (int r = 0; r <= KL; ++r) T[r] = make_double2(0.0, 0.0);
-                        // row j needs t_j, multipliers of column j, pivot j and (u, q_prev) at j + KL
-                        double2 nl[KL + 1], nt, nu = make_double2(0.0, 0.0), nqp = make_double2(0.0, 0.0);
+                        // row j needs t_j, multipliers of column j, pivot j and v_k, v_{k-1} at j + KL
+                        double2 nl[KL + 1], nt, nvc = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
                         int npv = 0;
                         auto load_e = [&](int j) {
                             nt = FLD(j, FX);
@@ -522,8 +549,8 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                                 for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
                             }
                             if (j + KL < n) {
-                                nu = FLD(j + KL, FB);
-                                nqp = first ? make_double2(0.0, 0.0) : FLD(j + KL, FA);
+                                nvc = FLD(j + KL, fcur);
+                                nvp = first ? make_double2(0.0, 0.0) : FLD(j + KL, fprv);
                             }
                         };
                         load_e(n - 1);
@@ -532,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 #pragma unroll
                             for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
                             const int cpv = npv;
-                            const double2 ct = nt, cu = nu, cqp = nqp;
+                            const double2 ct = nt, cvc = nvc, cvp = nvp;
                             if (j > 0) load_e(j - 1);
 #pragma unroll
                             for (int r = KL; r >= 1; --r) T[r] = T[r - 1];
@@ -547,16 +574,19 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                                     T[0] = s ? b : a;
                                     T[r] = s ? a : b;
                                 }
-                                if (j + KL < n) emit(j + KL, T[KL], cu, cqp);
+                                if (j + KL < n) emit(j + KL, T[KL], cvc, cvp);
                             } else {
-                                emit(j, T[0], cu, cqp);
+                                emit(j, T[0], cvc, cvp);
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < KL; ++r)
-                            if (r < n) emit(r, T[r], FLD(r, FB), first ? make_double2(0.0, 0.0) : FLD(r, FA));
+                            if (r < n) emit(r, T[r], FLD(r, fcur), first ? make_double2(0.0, 0.0) : FLD(r, fprv));
                     }
-                    alpha = asum;
+                    // alpha_k = Re<q_k, w_k> = asum / beta_{k-1} (asum at k = 1, v_1 = q_1);
+                    // v_{k+1} = w_k - alpha_k q_k = w_k - (alpha_k / beta_{k-1}) v_k
+                    const double alpha = first ? asum : asum * invb;
+                    acoef = first ? alpha : alpha * invb;
                     Ta[(int64_t)(k - 1) * TS] = alpha;
                     ksteps = k;
 
@@ -564,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                     if (k >= kr0) {
                         double th;
                         if (k == 1) th = alpha;
-                        else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, b2);
+                        else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, beta_p * beta_p);
                         else th = ritz_top_cold(Ta, Tb, TS, k);
                         const bool have_prev = (kth == k - 1);
                         theta_prev = theta;
