@@ -108,15 +108,19 @@ psa_lanczos_opts psa_default_opts(void);
 
 /* Bytes of device workspace that psa_sigma_min needs to keep
  * `points_in_flight` points in flight at once (rounded up to whole warps of
- * 32). The workspace holds a 256-byte flag block, the shared start vector
- * (n complex values) and one block per warp: for each of the n rows the
- * warp's pivoted band factor (2kl + ku + 1 complex values per point), three
- * Lanczos vectors and the pivot offsets, then the tridiagonal coefficients
- * (2 * k_max values per point). Host call, no device work.
+ * 32), for calls of up to `npoints` points (grid points, or list entries in
+ * restricted mode). The workspace holds a 256-byte flag block; the work-order
+ * schedule (8 KB plus 8 bytes per group of 32 points, at most npoints / 8 + 2
+ * groups); the shared start vector (n complex values); and one block per
+ * warp: for each of the n rows the warp's pivoted band factor (2kl + ku + 1
+ * complex values per point), three Lanczos vectors and the pivot offsets, then
+ * the tridiagonal coefficients (2 * k_max values per point). With npoints = 0
+ * the schedule is left out; psa_sigma_min then takes the groups in grid order,
+ * with the same results but a longer tail. Host call, no device work.
  * Errors: PSA_EINVAL for bad A fields (bands pointer may be NULL here),
- * bad opts, points_in_flight < 1 or bytes == NULL. */
+ * bad opts, points_in_flight < 1, npoints < 0 or bytes == NULL. */
 int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts,
-                        int64_t points_in_flight, size_t *bytes);
+                        int64_t points_in_flight, int64_t npoints, size_t *bytes);
 
 /* Points in flight that fill the current device once with the kernel for
  * A's band shape (SM count x resident blocks x 128 threads, from the CUDA
@@ -150,8 +154,12 @@ int psa_default_points_in_flight(const psa_band *A, int64_t npoints, int64_t *ou
  *           the number of points in flight (whole warps, at most one full
  *           occupancy of the device; see psa_workspace_bytes); it must not be
  *           used by another call that may run at the same time. Warps take
- *           groups of 32 consecutive points from a counter in the workspace,
- *           so the assignment of points to warps varies between calls while
+ *           groups of 32 points (8 x 4 grid tiles, or 32 list entries) from a
+ *           counter in the workspace. When the workspace has room for the
+ *           schedule, a short estimate pass (each group's anchor point, a few
+ *           Lanczos steps) first orders the groups by decreasing sigma, which
+ *           predicts the Lanczos step count, so the slowest groups start
+ *           first. The assignment of points to warps varies between calls;
  *           every point's arithmetic, and so its result, does not.
  *  stream   cudaStream_t to launch on.
  * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_EUNSUPPORTED, PSA_ECUDA. */

@@ -76,12 +76,15 @@ def _band_shape(n: int, kl: int, ku: int) -> _native.PsaBand:
 
 
 def workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
-                    opts: Optional[LanczosOpts] = None) -> int:
+                    opts: Optional[LanczosOpts] = None, npoints: int = 0) -> int:
+    """Workspace bytes for `points_in_flight` points in flight and calls of up to
+    `npoints` points (0: no work-order schedule)."""
     lib = _native.load()
     o = (opts or LanczosOpts())._c()
     out = ctypes.c_size_t()
     _native.check(lib.psa_workspace_bytes(ctypes.byref(_band_shape(n, kl, ku)), ctypes.byref(o),
-                                          int(points_in_flight), ctypes.byref(out)), "psa_workspace_bytes")
+                                          int(points_in_flight), int(npoints), ctypes.byref(out)),
+                  "psa_workspace_bytes")
     return int(out.value)
 
 
@@ -98,9 +101,9 @@ class Workspace:
     """Reusable device scratch for sigma_min (a torch uint8 buffer, 256-byte aligned)."""
 
     def __init__(self, n: int, kl: int, ku: int, points_in_flight: int,
-                 opts: Optional[LanczosOpts] = None, device=None):
+                 opts: Optional[LanczosOpts] = None, device=None, npoints: int = 0):
         import torch
-        self.nbytes = workspace_bytes(n, kl, ku, points_in_flight, opts)
+        self.nbytes = workspace_bytes(n, kl, ku, points_in_flight, opts, npoints)
         self.buffer = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
         base = self.buffer.data_ptr()
         self.offset = (-base) % 256
@@ -132,7 +135,7 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
     o = opts or LanczosOpts()
     if workspace is None:
         pif = points_in_flight or default_points_in_flight(n, kl, ku, max(npts, 1))
-        workspace = Workspace(n, kl, ku, pif, o, device=dev)
+        workspace = Workspace(n, kl, ku, pif, o, device=dev, npoints=npts)
     elif points_in_flight is not None:
         raise ValueError("pass either workspace or points_in_flight")
     if out is None:

@@ -75,7 +75,7 @@ def load(path: str | None = None):
         lib.psa_default_opts.restype = PsaLanczosOpts
         lib.psa_default_opts.argtypes = []
         lib.psa_workspace_bytes.restype = ctypes.c_int
-        lib.psa_workspace_bytes.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaLanczosOpts), i64,
+        lib.psa_workspace_bytes.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaLanczosOpts), i64, i64,
                                             ctypes.POINTER(ctypes.c_size_t)]
         lib.psa_default_points_in_flight.restype = ctypes.c_int
         lib.psa_default_points_in_flight.argtypes = [ctypes.POINTER(PsaBand), i64, ctypes.POINTER(i64)]

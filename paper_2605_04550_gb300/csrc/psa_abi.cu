@@ -13,31 +13,45 @@ namespace psa {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kEstimateSteps = 4;  // Lanczos steps of the work-order estimate
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace: [flags: 256 B][q1: n complex][per-warp blocks]. A warp block holds
-// n row records of row_bytes, then alpha_k and beta_k^2 for k_max steps (see the
-// kernel's header comment).
+// Workspace: [flags: 256 B][schedule][q1: n complex][per-warp blocks]. flags[0] marks
+// a non-finite band entry, flags[1] and flags[2] are the group counters of the main
+// and estimate passes. The schedule (optional) holds the bucket histogram and
+// cursors (kBuckets ints each), then one bucket and one order slot per group. A warp
+// block holds n row records of row_bytes, then alpha_k and beta_k^2 for k_max steps
+// (see the kernel's header comment).
 struct Layout {
-    size_t flags, q1, wdata, total;
+    size_t flags, sched, q1, wdata, total;
     int64_t warp_bytes;
     int row_bytes;
 };
 
 int row_bytes_of(int kl, int ku) { return (2 * kl + ku + 1 + 3) * 512 + 128; }
 
-Layout layout(int64_t n, int kl, int ku, int kmax, int64_t nwarps)
+size_t sched_bytes(int64_t ngroups)
+{
+    return ngroups > 0 ? align_up(sizeof(int) * (2 * (size_t)kBuckets + 2 * (size_t)ngroups)) : 0;
+}
+
+Layout layout(int64_t n, int kl, int ku, int kmax, int64_t nwarps, int64_t ngroups)
 {
     Layout L{};
     L.row_bytes = row_bytes_of(kl, ku);
     L.warp_bytes = (int64_t)align_up((size_t)n * L.row_bytes + 2 * (size_t)kmax * 32 * sizeof(double));
     size_t off = 0;
     L.flags = off; off += kAlign;
+    L.sched = off; off += sched_bytes(ngroups);
     L.q1 = off;    off += align_up(sizeof(double2) * (size_t)n);
     L.wdata = off; off += (size_t)nwarps * L.warp_bytes;
     L.total = off;
     return L;
 }
+
+// Upper bound on the groups of a call with `npoints` points: list chunks of 32, or
+// 8 x 4 tiles of an nx x ny grid (at most npoints / 8 + 2 of them).
+int64_t max_groups(int64_t npoints) { return npoints > 0 ? npoints / 8 + 2 : 0; }
 
 bool band_ok(const psa_band *A)
 {
@@ -99,6 +113,29 @@ __global__ void k_check_finite(const double2 *bands, int n, int kl, int ku, int 
         if (col < 0 || col >= n) continue;
         const double2 a = bands[e];
         if (!isfinite(a.x) || !isfinite(a.y)) atomicOr(flags, 1);
+    }
+}
+
+// cursor[b] = number of groups in buckets above b (descending order of buckets).
+__global__ void __launch_bounds__(1024) k_sched_scan(const int *hist, int *cursor)
+{
+    __shared__ int h[kBuckets];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = hist[b];
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+        int s = 0;
+        for (int c = b + 1; c < kBuckets; ++c) s += h[c];
+        cursor[b] = s;
+    }
+}
+
+// order[slot] = group, groups of higher buckets first (order within a bucket is
+// immaterial: it changes which warp takes a group, never a point's result).
+__global__ void k_sched_scatter(const int *bucket, int *cursor, int *order, int64_t ngroups)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < ngroups; a += (int64_t)gridDim.x * blockDim.x) {
+        const int b = bucket[a] & (kBuckets - 1);
+        order[atomicAdd(&cursor[b], 1)] = (int)a;
     }
 }
 
@@ -188,13 +225,14 @@ psa_lanczos_opts psa_default_opts(void)
     return o;
 }
 
-int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts, int64_t points_in_flight, size_t *bytes)
+int psa_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts, int64_t points_in_flight, int64_t npoints,
+                        size_t *bytes)
 {
-    if (!band_ok(A) || points_in_flight < 1 || !bytes) return PSA_EINVAL;
+    if (!band_ok(A) || points_in_flight < 1 || npoints < 0 || !bytes) return PSA_EINVAL;
     const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
     if (!opts_ok(o)) return PSA_EINVAL;
     const int64_t nwarps = (points_in_flight + 31) / 32;
-    *bytes = layout(A->n, A->kl, A->ku, o.k_max, nwarps).total;
+    *bytes = layout(A->n, A->kl, A->ku, o.k_max, nwarps, max_groups(npoints)).total;
     return PSA_OK;
 }
 
@@ -238,17 +276,21 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     const int64_t n = A->n;
     // points in flight: whole warps, as many as the workspace holds, at most one
     // full occupancy of the device and no more than the points to evaluate
-    const Layout L1 = layout(n, A->kl, A->ku, o.k_max, 1);
+    const int64_t ngroups = idx ? (npts + 31) / 32 : (int64_t)((g->nx + 7) / 8) * ((g->ny + 3) / 4);
+    const Layout L1 = layout(n, A->kl, A->ku, o.k_max, 1, 0);
     if (L1.total > ws_bytes) return PSA_EWORKSPACE;
-    int64_t nwarps = (int64_t)((ws_bytes - (L1.total - (size_t)L1.warp_bytes)) / (size_t)L1.warp_bytes);
+    // the longest-first work order needs the schedule arrays; without room for them
+    // (a workspace sized for no points) warps take the groups in grid order
+    const bool ordered = layout(n, A->kl, A->ku, o.k_max, 1, ngroups).total <= ws_bytes && ngroups > 1;
+    const size_t sched = ordered ? sched_bytes(ngroups) : 0;
+    int64_t nwarps = (int64_t)((ws_bytes - sched - (L1.total - (size_t)L1.warp_bytes)) / (size_t)L1.warp_bytes);
     int64_t full = 0;
     const int frc = full_threads(ops, &full);
     if (frc != PSA_OK) return frc;
     if (nwarps > full / 32) nwarps = full / 32;
-    const int64_t need_w = idx ? (npts + 31) / 32 : (int64_t)((g->nx + 7) / 8) * ((g->ny + 3) / 4);
-    if (nwarps > need_w) nwarps = need_w < 1 ? 1 : need_w;
+    if (nwarps > ngroups) nwarps = ngroups < 1 ? 1 : ngroups;
     if (nwarps >= 4) nwarps = round_down(nwarps, 4);
-    const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps);
+    const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps, ordered ? ngroups : 0);
     const int64_t P = nwarps * 32;
 
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
@@ -267,7 +309,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.ny = g->ny;
     p.idx = idx;
     p.npts = npts;
-    p.ngroups = idx ? (npts + 31) / 32 : (int64_t)((g->nx + 7) / 8) * ((g->ny + 3) / 4);
+    p.ngroups = ngroups;
     for (int l = 0; l < kMaxEps; ++l) p.eps[l] = l < n_eps ? eps[l] : 0.0;
     p.n_eps = n_eps;
     p.k_min = o.k_min;
@@ -279,6 +321,14 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.steps = steps;
     p.flags = reinterpret_cast<const int *>(ws + L.flags);
     p.counter = reinterpret_cast<int *>(ws + L.flags) + 1;
+    int *const hist = reinterpret_cast<int *>(ws + L.sched);
+    int *const cursor = hist + kBuckets;
+    int *const bucket = cursor + kBuckets;
+    int *const order = bucket + ngroups;
+    p.estimate = 0;
+    p.order = ordered ? order : nullptr;
+    p.sched_bucket = bucket;
+    p.sched_hist = hist;
     p.q1 = reinterpret_cast<const double2 *>(ws + L.q1);
     p.wdata = ws + L.wdata;
     p.warp_bytes = L.warp_bytes;
@@ -304,6 +354,27 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
         if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
     }
     if (npts == 0) return PSA_OK;
+    if (ordered) {
+        // estimate pass: each group's anchor point, LU + a few Lanczos steps, then the
+        // groups sorted into decreasing buckets of log2(sigma estimate)
+        if (cudaMemsetAsync(hist, 0, sizeof(int) * kBuckets, stream) != cudaSuccess) return PSA_ECUDA;
+        KParams pe = p;
+        pe.estimate = 1;
+        pe.order = nullptr;
+        pe.k_min = pe.k_max = o.k_max < kEstimateSteps ? o.k_max : kEstimateSteps;
+        pe.tol = 0.0;
+        pe.counter = reinterpret_cast<int *>(ws + L.flags) + 2;
+        pe.sigma = nullptr;
+        pe.mask = nullptr;
+        pe.status = nullptr;
+        pe.steps = nullptr;
+        if (ops.launch(pe, stream) != cudaSuccess) return PSA_ECUDA;
+        k_sched_scan<<<1, 1024, 0, stream>>>(hist, cursor);
+        if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+        const int64_t sb = (ngroups + 255) / 256 < 4096 ? (ngroups + 255) / 256 : 4096;
+        k_sched_scatter<<<(unsigned)sb, 256, 0, stream>>>(bucket, cursor, order, ngroups);
+        if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+    }
     if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
     return PSA_OK;
 }

@@ -10,6 +10,7 @@ constexpr int kMaxEps = 32;
 constexpr int kThreads = 128;        // threads per block of the sigma_min kernel
 constexpr int kMaxKL = 4;            // compile-time band shapes: kl in [0, 4]
 constexpr int kMaxKU = 8;            //                           ku in [0, 8]
+constexpr int kBuckets = 1024;       // log2-sigma buckets of the work order (8 per octave)
 
 // Everything one launch of the sigma_min kernel needs (passed by value).
 struct KParams {
@@ -23,6 +24,13 @@ struct KParams {
     const int32_t *idx;
     int64_t npts;
     int64_t ngroups;  // groups of 32 points: 8 x 4 grid tiles (full grid) or list chunks
+    // work order: estimate != 0 runs only each group's anchor point for k_max steps
+    // and files the group under a bucket of log2 sigma (sched_bucket, sched_hist);
+    // otherwise warps take groups order[0], order[1], ... (or 0, 1, ... if order is NULL)
+    int estimate;
+    const int *order;
+    int *sched_bucket;
+    int *sched_hist;
     // epsilon levels
     double eps[kMaxEps];
     int n_eps;

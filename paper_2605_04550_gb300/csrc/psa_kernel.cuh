@@ -39,7 +39,10 @@
 // take more of them. On the full grid a group is an 8 x 4 tile of the grid
 // (neighbouring points converge in similar step counts, so fewer lanes idle
 // than with 32 points of one grid row); in restricted mode it is 32
-// consecutive entries of the list. Each warp owns one contiguous workspace block.
+// consecutive entries of the list. A short estimate pass (one anchor point per
+// group, a few Lanczos steps) lets the groups be taken longest first, so the
+// launch does not end on a few slow groups. Each warp owns one contiguous
+// workspace block.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -222,6 +225,38 @@ struct Shape {
     static constexpr int MIN_BLOCKS = ((KL + 1) * (KW + 1) <= 24) ? 3 : 2;
 };
 
+// Flat grid index of lane `lane` of group g (-1: no point): on the full grid an
+// 8 x 4 tile (8 abscissae, 4 ordinates), whose neighbouring points take similar
+// Lanczos step counts so the warp's lanes stay busy together; in restricted mode
+// 32 consecutive entries of the list.
+__device__ __forceinline__ int64_t group_point(const KParams &p, int64_t g, int lane, int64_t ngrid)
+{
+    if (p.idx) {
+        const int64_t pt = g * 32 + lane;
+        if (pt >= p.npts) return -1;
+        const int64_t f = (int64_t)p.idx[pt];
+        return (f >= 0 && f < ngrid) ? f : -1;
+    }
+    const int tiles_x = (p.nx + 7) >> 3;
+    const int ty = (int)(g / tiles_x), tx = (int)(g - (int64_t)ty * tiles_x);
+    const int i = ty * 4 + (lane >> 3), j = tx * 8 + (lane & 7);
+    return (i < p.ny && j < p.nx) ? (int64_t)i * p.nx + j : -1;
+}
+
+// A point representative of group g for the work-order estimate: the tile's point
+// (1, 3) (clamped to the grid), or the first entry of a list chunk.
+__device__ __forceinline__ int64_t group_anchor(const KParams &p, int64_t g, int64_t ngrid)
+{
+    if (p.idx) {
+        const int64_t f = (int64_t)p.idx[g * 32];
+        return (f >= 0 && f < ngrid) ? f : -1;
+    }
+    const int tiles_x = (p.nx + 7) >> 3;
+    const int ty = (int)(g / tiles_x), tx = (int)(g - (int64_t)ty * tiles_x);
+    const int i = min(ty * 4 + 1, p.ny - 1), j = min(tx * 8 + 3, p.nx - 1);
+    return (int64_t)i * p.nx + j;
+}
+
 template <int KL, int KU>
 __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_min(const KParams p)
 {
@@ -248,30 +283,30 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 #define PIVOF(j) (pivs[(j) * RB])
 
     for (;;) {
-        // the warp takes the next group of 32 points
+        // the warp takes the next group of 32 points (estimate pass: 32 groups' anchors)
         int grp = 0;
         if (lane == 0) grp = atomicAdd(p.counter, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
-        if (grp >= p.ngroups) break;
+        if ((int64_t)grp >= (p.estimate ? (p.ngroups + 31) / 32 : p.ngroups)) break;
         int64_t flat = -1;
-        if (p.idx) {
-            // restricted mode: 32 consecutive entries of the list
-            const int64_t pt = (int64_t)grp * 32 + lane;
-            if (pt < p.npts) {
-                flat = (int64_t)p.idx[pt];
-                if (flat >= ngrid) flat = -1;
+        int64_t anchor_of = -1;  // estimate pass: the group whose anchor this lane runs
+        if (p.estimate) {
+            const int64_t a = (int64_t)grp * 32 + lane;
+            if (a < p.ngroups) {
+                anchor_of = a;
+                flat = group_anchor(p, a, ngrid);
             }
         } else {
-            // full grid: an 8 x 4 tile (8 abscissae, 4 ordinates); neighbouring points
-            // take similar Lanczos step counts, so the warp's lanes stay busy together
-            const int tiles_x = (p.nx + 7) >> 3;
-            const int ty = (int)(grp / tiles_x), tx = (int)(grp - (int64_t)ty * tiles_x);
-            const int i = ty * 4 + (lane >> 3), j = tx * 8 + (lane & 7);
-            if (i < p.ny && j < p.nx) flat = (int64_t)i * p.nx + j;
+            const int64_t g = p.order ? (int64_t)p.order[grp] : (int64_t)grp;
+            flat = group_point(p, g, lane, ngrid);
         }
         // every lane runs the factorisation (lanes without a point on a dummy z), so
         // that the warp can stage the bands of A cooperatively
         const bool have = flat >= 0;
+        if (p.estimate && anchor_of >= 0 && !have) {  // no valid anchor: file the group first-to-last
+            p.sched_bucket[anchor_of] = 0;
+            atomicAdd(&p.sched_hist[0], 1);
+        }
         {
             const int gi = have ? (int)(flat / p.nx) : 0;
             const int gj = have ? (int)(flat - (int64_t)gi * p.nx) : 0;
@@ -620,6 +655,18 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
             }
 
             // ---------------- 4. outputs
+            if (p.estimate) {
+                // file the group under log2(sigma estimate), 8 buckets per octave; points
+                // far from the spectrum take the most Lanczos steps, so groups are later
+                // taken in decreasing bucket order (longest first)
+                int b = 0;
+                if ((status == 0 || status == 2) && sigma > 0.0)
+                    b = clampi(8 * (exp_field(sigma) - 1023) + ((__double2hiint(sigma) >> 17) & 7) + kBuckets / 2, 1,
+                               kBuckets - 1);
+                p.sched_bucket[anchor_of] = b;
+                atomicAdd(&p.sched_hist[b], 1);
+                continue;
+            }
             p.sigma[flat] = sigma;
             if (p.mask) {
                 uint32_t bits = 0;

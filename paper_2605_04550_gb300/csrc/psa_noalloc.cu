@@ -47,7 +47,7 @@ extern "C" int psa_sigma_min_static(const psa_band *A, const psa_grid *g, const 
 {
     // the problem must fit the fixed scratch with at least one warp (32 points) in flight
     size_t need = 0;
-    const int rc = psa_workspace_bytes(A, opts, 32, &need);
+    const int rc = psa_workspace_bytes(A, opts, 32, 0, &need);
     if (rc != PSA_OK) return rc;
     if (need > (size_t)PSA_STATIC_SCRATCH_BYTES) return PSA_ESTATIC;
     void *scratch = nullptr;

@@ -46,10 +46,10 @@ def test_default_opts(lib):
     assert (o.k_min, o.k_max, o.tol, o.seed) == (2, 1000, 1e-13, 0)
 
 
-def _ws(lib, n, kl, ku, P, kmax=1000):
+def _ws(lib, n, kl, ku, P, kmax=1000, npoints=0):
     out = ctypes.c_size_t()
     o = _native.PsaLanczosOpts(2, kmax, 1e-13, 0)
-    rc = lib.psa_workspace_bytes(ctypes.byref(_native.PsaBand(n, kl, ku, None)), ctypes.byref(o), P,
+    rc = lib.psa_workspace_bytes(ctypes.byref(_native.PsaBand(n, kl, ku, None)), ctypes.byref(o), P, npoints,
                                  ctypes.byref(out))
     return rc, out.value
 
@@ -65,11 +65,16 @@ def test_workspace_bytes_layout(lib):
     assert expect <= b <= expect + (P // 32) * (n * (128 - 32) + 256) + 256
     # rounded up to whole warps
     assert _ws(lib, 2000, 2, 5, 97)[1] == _ws(lib, 2000, 2, 5, 128)[1]
+    # the work-order schedule: 8 KB + 8 bytes per group, at most npoints / 8 + 2 groups
+    npts = 262144
+    extra = _ws(lib, 2000, 2, 5, 128, npoints=npts)[1] - b
+    assert 8192 + 8 * (npts // 8 + 2) <= extra <= 8192 + 8 * (npts // 8 + 2) + 256
 
 
-@pytest.mark.parametrize("n,kl,ku,P", [(0, 0, 0, 32), (5, 5, 0, 32), (5, 0, 5, 32), (5, -1, 0, 32), (5, 1, 1, 0)])
-def test_workspace_bytes_rejects(lib, n, kl, ku, P):
-    assert _ws(lib, n, kl, ku, P)[0] == _native.PSA_EINVAL
+@pytest.mark.parametrize("n,kl,ku,P,npts", [(0, 0, 0, 32, 0), (5, 5, 0, 32, 0), (5, 0, 5, 32, 0), (5, -1, 0, 32, 0),
+                                            (5, 1, 1, 0, 0), (5, 1, 1, 32, -1)])
+def test_workspace_bytes_rejects(lib, n, kl, ku, P, npts):
+    assert _ws(lib, n, kl, ku, P, npoints=npts)[0] == _native.PSA_EINVAL
 
 
 def _call(lib, *, n=10, kl=1, ku=1, bands=1 << 20, grid=(-1.0, 1.0, -1.0, 1.0, 4, 4), eps=(0.1,),
