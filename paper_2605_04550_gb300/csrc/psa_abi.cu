@@ -281,7 +281,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     if (L1.total > ws_bytes) return PSA_EWORKSPACE;
     // the longest-first work order needs the schedule arrays; without room for them
     // (a workspace sized for no points) warps take the groups in grid order
-    const bool ordered = layout(n, A->kl, A->ku, o.k_max, 1, ngroups).total <= ws_bytes && ngroups > 1;
+    bool ordered = layout(n, A->kl, A->ku, o.k_max, 1, ngroups).total <= ws_bytes && ngroups > 1;
     const size_t sched = ordered ? sched_bytes(ngroups) : 0;
     int64_t nwarps = (int64_t)((ws_bytes - sched - (L1.total - (size_t)L1.warp_bytes)) / (size_t)L1.warp_bytes);
     int64_t full = 0;
@@ -289,6 +289,8 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     if (frc != PSA_OK) return frc;
     if (nwarps > full / 32) nwarps = full / 32;
     if (nwarps > ngroups) nwarps = ngroups < 1 ? 1 : ngroups;
+    // the estimate pass pays off when warps take several groups each (a long tail)
+    if (ordered && ngroups < 4 * nwarps) ordered = false;
     if (nwarps >= 4) nwarps = round_down(nwarps, 4);
     const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps, ordered ? ngroups : 0);
     const int64_t P = nwarps * 32;
