@@ -170,6 +170,42 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g,
                   const psa_lanczos_opts *opts,
                   void *workspace, size_t ws_bytes, void *stream);
 
+/* Bytes of device workspace for psa_sigma_min_grad with `points_in_flight`
+ * points in flight (whole warps): like psa_workspace_bytes with a fourth vector
+ * per row (the Ritz vector) and four tridiagonal arrays per point, no schedule.
+ * Host call. Errors: PSA_EINVAL. */
+int psa_grad_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts,
+                             int64_t points_in_flight, size_t *bytes);
+
+/* sigma_min(zI - A) and its adjoint gradients at n_pts explicit points z.
+ *
+ * For a simple smallest singular value with singular vectors u, v of
+ * B = zI - A (B v = sigma u), d sigma = Re(u^* dB v), so
+ *   grad_z[p]  = d sigma_p / d Re z + i d sigma_p / d Im z = conj(u^* v),
+ *   grad_bands = sum_p weight[p] (d sigma_p / d Re a + i d sigma_p / d Im a)
+ *              = -sum_p weight[p] u_i conj(v_{i+d})  for a = A[i][i+d],
+ * in band storage (bands[(d + kl) * n + i]). These are the derivatives that the
+ * Newton refinement of eps-contours (paper Sec. 2, Definition "Pseudospectrum")
+ * and a torch.autograd backward need. u is the Ritz vector of the converged
+ * Lanczos process (a second pass replays the recurrence), v = B^{-1} u / |B^{-1} u|.
+ *
+ *  A, opts        as psa_sigma_min (kl <= 4, ku <= 8).
+ *  z              DEVICE, n_pts complex points (any, not only grid points).
+ *  weight         DEVICE, n_pts upstream weights; required when grad_bands != NULL.
+ *  sigma          DEVICE output, n_pts doubles (required if n_pts > 0).
+ *  grad_z         DEVICE output, n_pts complex (may be NULL). 0 where status is
+ *                 not OK / NOT_CONVERGED or sigma = 0.
+ *  grad_bands     DEVICE output, (kl + ku + 1) * n complex, zeroed and then summed
+ *                 into (may be NULL; the sum's order varies between runs).
+ *  status, steps  DEVICE outputs per point (may be NULL), codes as psa_sigma_min.
+ *  workspace      DEVICE scratch, 256-byte aligned, of ws_bytes (psa_grad_workspace_bytes).
+ * Asynchronous on `stream`; allocates nothing.
+ * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_EUNSUPPORTED, PSA_ECUDA. */
+int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const double *weight,
+                       double *sigma, psa_c64 *grad_z, psa_c64 *grad_bands,
+                       int8_t *status, int32_t *steps, const psa_lanczos_opts *opts,
+                       void *workspace, size_t ws_bytes, void *stream);
+
 /* Size of the fixed device scratch used by psa_sigma_min_static (64 MiB). */
 #define PSA_STATIC_SCRATCH_BYTES (64u << 20)
 

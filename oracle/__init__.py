@@ -241,3 +241,35 @@ def sigma_min_grid(bands: np.ndarray, kl: int, ku: int, grid, eps: Sequence[floa
     s, st, k = sigma_min_banded(bands, kl, ku, z.ravel(), **kw)
     shp = (grid.ny, grid.nx)
     return s.reshape(shp), masks(s, eps).reshape(shp), st.reshape(shp), k.reshape(shp)
+
+
+# ------------------------------------------------------------ gradients
+def sigma_min_grad_dense(A: np.ndarray, z: complex):
+    """sigma_min(zI - A) and its first derivatives from a dense SVD.
+
+    For a simple smallest singular value with B v = sigma u (B = zI - A),
+    d sigma = Re(u^* dB v) (first-order perturbation of a singular value), so
+      grad_z = d sigma / d Re z + i d sigma / d Im z = conj(u^* v)
+      grad_A[i, j] = d sigma / d Re A_ij + i d sigma / d Im A_ij = -u_i conj(v_j).
+    Returns (sigma, grad_z, grad_A) with grad_A dense (n x n).
+    """
+    A = np.asarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    B = complex(z) * np.eye(n) - A
+    U, s, Vh = np.linalg.svd(B)
+    u = U[:, -1]
+    v = Vh[-1].conj()
+    gz = np.conj(np.vdot(u, v))
+    gA = -np.outer(u, v.conj())
+    return float(s[-1]), complex(gz), gA
+
+
+def dense_grad_to_bands(gA: np.ndarray, kl: int, ku: int) -> np.ndarray:
+    """The band part of a dense gradient, in band storage g[d + kl, i] = gA[i, i + d]."""
+    n = gA.shape[0]
+    g = np.zeros((kl + ku + 1, n), dtype=np.complex128)
+    for d in range(-kl, ku + 1):
+        for i in range(n):
+            if 0 <= i + d < n:
+                g[d + kl, i] = gA[i, i + d]
+    return g

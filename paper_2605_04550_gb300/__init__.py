@@ -27,6 +27,7 @@ from .inputs import Grid
 __all__ = [
     "Grid", "LanczosOpts", "SigmaMinResult", "Workspace", "sigma_min", "workspace_bytes",
     "default_points_in_flight", "probe_dfma_rate", "library_path", "PsaError", "tile_order",
+    "SigmaMinGradResult", "sigma_min_grad", "grad_workspace_bytes", "SigmaMinFunction", "sigma_min_autograd",
     "PT_OK", "PT_SINGULAR", "PT_NOT_CONVERGED", "PT_NONFINITE", "PT_NOT_EVALUATED", "PT_UNDERFLOW",
 ]
 
@@ -159,6 +160,64 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
     return out
 
 
+@dataclasses.dataclass
+class SigmaMinGradResult:
+    sigma: "object"       # torch.float64 (npts,)
+    grad_z: "object"      # torch.complex128 (npts,): d sigma / d Re z + i d sigma / d Im z
+    grad_bands: "object"  # torch.complex128 (kl + ku + 1, n) or None
+    status: "object"      # torch.int8 (npts,)
+    steps: "object"       # torch.int32 (npts,)
+
+
+def grad_workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
+                         opts: Optional[LanczosOpts] = None) -> int:
+    lib = _native.load()
+    o = (opts or LanczosOpts())._c()
+    out = ctypes.c_size_t()
+    _native.check(lib.psa_grad_workspace_bytes(ctypes.byref(_band_shape(n, kl, ku)), ctypes.byref(o),
+                                               int(points_in_flight), ctypes.byref(out)), "psa_grad_workspace_bytes")
+    return int(out.value)
+
+
+def sigma_min_grad(bands, kl: int, ku: int, z, weight=None, opts: Optional[LanczosOpts] = None,
+                   points_in_flight: Optional[int] = None, stream=None) -> SigmaMinGradResult:
+    """sigma_min(z I - A) at explicit points with its adjoint gradients (psa_sigma_min_grad).
+
+    z: CUDA complex128 tensor of points. weight: optional CUDA float64 tensor of
+    upstream weights; when given, grad_bands = sum_p weight_p d sigma_p / d bands.
+    """
+    import torch
+    lib = _native.load()
+    A = _band(bands, kl, ku)
+    n = A.n
+    dev = bands.device
+    if not isinstance(z, torch.Tensor) or z.dtype != torch.complex128 or not z.is_cuda:
+        raise TypeError("z must be a CUDA complex128 tensor")
+    zc = z.contiguous().reshape(-1)
+    npts = int(zc.numel())
+    o = opts or LanczosOpts()
+    if weight is not None:
+        weight = weight.to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
+        if weight.numel() != npts:
+            raise ValueError("weight must have one entry per point")
+    pif = points_in_flight or min(default_points_in_flight(n, kl, ku, max(npts, 1)), max(32, -(-npts // 32) * 32))
+    nbytes = grad_workspace_bytes(n, kl, ku, pif, o)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    ptr = buf.data_ptr() + ((-buf.data_ptr()) % 256)
+    sigma = torch.empty(npts, dtype=torch.float64, device=dev)
+    gz = torch.empty(npts, dtype=torch.complex128, device=dev)
+    gb = torch.empty((kl + ku + 1, n), dtype=torch.complex128, device=dev) if weight is not None else None
+    status = torch.empty(npts, dtype=torch.int8, device=dev)
+    steps = torch.empty(npts, dtype=torch.int32, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = lib.psa_sigma_min_grad(ctypes.byref(A), zc.data_ptr() if npts else None, npts,
+                                weight.data_ptr() if weight is not None else None,
+                                sigma.data_ptr(), gz.data_ptr(), gb.data_ptr() if gb is not None else None,
+                                status.data_ptr(), steps.data_ptr(), ctypes.byref(o._c()), ptr, nbytes, s.cuda_stream)
+    _native.check(rc, "psa_sigma_min_grad")
+    return SigmaMinGradResult(sigma, gz, gb, status, steps)
+
+
 def tile_order(flat_idx, nx: int):
     """Flat grid indices reordered into 8 x 4 tiles (the full-grid work order).
 
@@ -181,3 +240,48 @@ def probe_dfma_rate(iters: int = 4096, stream=None) -> float:
     s = stream if stream is not None else torch.cuda.current_stream()
     _native.check(lib.psa_probe_dfma_rate(int(iters), ctypes.byref(out), s.cuda_stream), "psa_probe_dfma_rate")
     return float(out.value)
+
+
+def _make_autograd():
+    import torch
+
+    class SigmaMinFunction(torch.autograd.Function):
+        """sigma_min(z I - A) as a differentiable function of the band entries and z.
+
+        forward(bands, z, kl, ku, opts) -> sigma (float64, shape of z); backward uses the
+        adjoint kernel (psa_sigma_min_grad) with the upstream gradient as weights:
+        d/d bands = sum_p g_p d sigma_p / d bands, d/d z_p = g_p d sigma_p / d z
+        (PyTorch's convention for complex inputs: d/d Re + i d/d Im).
+        """
+
+        @staticmethod
+        def forward(ctx, bands, z, kl, ku, opts=None):
+            r = sigma_min_grad(bands.detach(), kl, ku, z.detach(), weight=None, opts=opts)
+            ctx.save_for_backward(bands.detach(), z.detach(), r.grad_z)
+            ctx.kl, ctx.ku, ctx.opts = kl, ku, opts
+            return r.sigma.reshape(z.shape)
+
+        @staticmethod
+        def backward(ctx, g):
+            bands, z, gz = ctx.saved_tensors
+            gflat = g.reshape(-1).to(torch.float64).contiguous()
+            grad_bands = grad_z = None
+            if ctx.needs_input_grad[0]:
+                r = sigma_min_grad(bands, ctx.kl, ctx.ku, z, weight=gflat, opts=ctx.opts)
+                grad_bands = r.grad_bands
+            if ctx.needs_input_grad[1]:
+                grad_z = (gz * gflat).reshape(z.shape)
+            return grad_bands, grad_z, None, None, None
+
+    return SigmaMinFunction
+
+
+def __getattr__(name):
+    if name == "SigmaMinFunction":
+        return _make_autograd()
+    raise AttributeError(name)
+
+
+def sigma_min_autograd(bands, z, kl: int, ku: int, opts: Optional[LanczosOpts] = None):
+    """Differentiable sigma_min(z I - A) (see SigmaMinFunction)."""
+    return _make_autograd().apply(bands, z, kl, ku, opts)

@@ -26,6 +26,8 @@ EXPORTS = (
     "psa_default_points_in_flight",
     "psa_sigma_min",
     "psa_sigma_min_static",
+    "psa_grad_workspace_bytes",
+    "psa_sigma_min_grad",
     "psa_probe_dfma_rate",
 )
 
@@ -87,6 +89,12 @@ def load(path: str | None = None):
         lib.psa_sigma_min_static.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaGrid),
                                              ctypes.POINTER(dbl), i32, vp, i64, vp, vp, vp, vp,
                                              ctypes.POINTER(PsaLanczosOpts), vp]
+        lib.psa_grad_workspace_bytes.restype = ctypes.c_int
+        lib.psa_grad_workspace_bytes.argtypes = [ctypes.POINTER(PsaBand), ctypes.POINTER(PsaLanczosOpts), i64,
+                                                 ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_sigma_min_grad.restype = ctypes.c_int
+        lib.psa_sigma_min_grad.argtypes = [ctypes.POINTER(PsaBand), vp, i64, vp, vp, vp, vp, vp, vp,
+                                           ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         _lib = lib

@@ -28,18 +28,20 @@ struct Layout {
     int row_bytes;
 };
 
-int row_bytes_of(int kl, int ku) { return (2 * kl + ku + 1 + 3) * 512 + 128; }
+// Row record: S = 2kl+ku+1 factor fields and nvec Lanczos vector fields of 512 bytes,
+// then 32 pivot bytes (padded to 128).
+int row_bytes_of(int kl, int ku, int nvec = 3) { return (2 * kl + ku + 1 + nvec) * 512 + 128; }
 
 size_t sched_bytes(int64_t ngroups)
 {
     return ngroups > 0 ? align_up(sizeof(int) * (2 * (size_t)kBuckets + 2 * (size_t)ngroups)) : 0;
 }
 
-Layout layout(int64_t n, int kl, int ku, int kmax, int64_t nwarps, int64_t ngroups)
+Layout layout(int64_t n, int kl, int ku, int kmax, int64_t nwarps, int64_t ngroups, int nvec = 3, int ntri = 2)
 {
     Layout L{};
-    L.row_bytes = row_bytes_of(kl, ku);
-    L.warp_bytes = (int64_t)align_up((size_t)n * L.row_bytes + 2 * (size_t)kmax * 32 * sizeof(double));
+    L.row_bytes = row_bytes_of(kl, ku, nvec);
+    L.warp_bytes = (int64_t)align_up((size_t)n * L.row_bytes + (size_t)ntri * (size_t)kmax * 32 * sizeof(double));
     size_t off = 0;
     L.flags = off; off += kAlign;
     L.sched = off; off += sched_bytes(ngroups);
@@ -178,6 +180,18 @@ KernelOps pick_ops(int kl, int ku)
     case 2: return kernel_ops_kl2(ku);
     case 3: return kernel_ops_kl3(ku);
     case 4: return kernel_ops_kl4(ku);
+    default: return KernelOps{nullptr, nullptr};
+    }
+}
+
+KernelOps pick_grad_ops(int kl, int ku)
+{
+    switch (kl) {
+    case 0: return grad_ops_kl0(ku);
+    case 1: return grad_ops_kl1(ku);
+    case 2: return grad_ops_kl2(ku);
+    case 3: return grad_ops_kl3(ku);
+    case 4: return grad_ops_kl4(ku);
     default: return KernelOps{nullptr, nullptr};
     }
 }
@@ -335,6 +349,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.wdata = ws + L.wdata;
     p.warp_bytes = L.warp_bytes;
     p.row_bytes = L.row_bytes;
+    p.piv_offset = (2 * A->kl + A->ku + 1 + 3) * 512;
     p.P = P;
 
     if (mask && n_eps == 0) {
@@ -377,6 +392,90 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
         k_sched_scatter<<<(unsigned)sb, 256, 0, stream>>>(bucket, cursor, order, ngroups);
         if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
     }
+    if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
+    return PSA_OK;
+}
+
+int psa_grad_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts, int64_t points_in_flight, size_t *bytes)
+{
+    if (!band_ok(A) || points_in_flight < 1 || !bytes) return PSA_EINVAL;
+    const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
+    if (!opts_ok(o)) return PSA_EINVAL;
+    const int64_t nwarps = (points_in_flight + 31) / 32;
+    *bytes = layout(A->n, A->kl, A->ku, o.k_max, nwarps, 0, 4, 4).total;
+    return PSA_OK;
+}
+
+int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const double *weight, double *sigma,
+                       psa_c64 *grad_z, psa_c64 *grad_bands, int8_t *status, int32_t *steps,
+                       const psa_lanczos_opts *opts, void *workspace, size_t ws_bytes, void *stream_ptr)
+{
+    if (!band_ok(A) || !A->bands || n_pts < 0 || (n_pts > 0 && (!z || !sigma))) return PSA_EINVAL;
+    if (grad_bands && !weight) return PSA_EINVAL;
+    const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
+    if (!opts_ok(o)) return PSA_EINVAL;
+    if (A->kl > kMaxKL || A->ku > kMaxKU || (int64_t)A->n * row_bytes_of(A->kl, A->ku, 4) >= 2147483647LL)
+        return PSA_EUNSUPPORTED;
+    const KernelOps ops = pick_grad_ops(A->kl, A->ku);
+    if (!ops.launch) return PSA_EUNSUPPORTED;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PSA_EWORKSPACE;
+    const int64_t n = A->n;
+    const Layout L1 = layout(n, A->kl, A->ku, o.k_max, 1, 0, 4, 4);
+    if (L1.total > ws_bytes) return PSA_EWORKSPACE;
+    int64_t nwarps = (int64_t)((ws_bytes - (L1.total - (size_t)L1.warp_bytes)) / (size_t)L1.warp_bytes);
+    int64_t full = 0;
+    const int frc = full_threads(ops, &full);
+    if (frc != PSA_OK) return frc;
+    if (nwarps > full / 32) nwarps = full / 32;
+    const int64_t ngroups = (n_pts + 31) / 32;
+    if (nwarps > ngroups) nwarps = ngroups < 1 ? 1 : ngroups;
+    if (nwarps >= 4) nwarps = round_down(nwarps, 4);
+    const Layout L = layout(n, A->kl, A->ku, o.k_max, nwarps, 0, 4, 4);
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    char *ws = static_cast<char *>(workspace);
+
+    KParams p{};
+    p.bands = reinterpret_cast<const double2 *>(A->bands);
+    p.n = A->n;
+    p.kl = A->kl;
+    p.ku = A->ku;
+    p.nx = 1;
+    p.ny = 1;
+    p.npts = n_pts;
+    p.ngroups = ngroups;
+    p.k_min = o.k_min;
+    p.k_max = o.k_max;
+    p.tol = o.tol;
+    p.zpts = reinterpret_cast<const double2 *>(z);
+    p.gweight = weight;
+    p.grad_z = reinterpret_cast<double2 *>(grad_z);
+    p.grad_bands = reinterpret_cast<double2 *>(grad_bands);
+    p.sigma = sigma;
+    p.status = status;
+    p.steps = steps;
+    p.flags = reinterpret_cast<const int *>(ws + L.flags);
+    p.counter = reinterpret_cast<int *>(ws + L.flags) + 1;
+    p.q1 = reinterpret_cast<const double2 *>(ws + L.q1);
+    p.wdata = ws + L.wdata;
+    p.warp_bytes = L.warp_bytes;
+    p.row_bytes = L.row_bytes;
+    p.piv_offset = (2 * A->kl + A->ku + 1 + 4) * 512;
+    p.P = nwarps * 32;
+
+    if (grad_bands &&
+        cudaMemsetAsync(grad_bands, 0, sizeof(psa_c64) * (size_t)(A->kl + A->ku + 1) * (size_t)n, stream) != cudaSuccess)
+        return PSA_ECUDA;
+    k_start_vector<<<1, 256, 0, stream>>>(reinterpret_cast<double2 *>(ws + L.q1), A->n, o.seed);
+    if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+    if (cudaMemsetAsync(ws + L.flags, 0, kAlign, stream) != cudaSuccess) return PSA_ECUDA;
+    {
+        const int64_t total = (int64_t)(A->kl + A->ku + 1) * A->n;
+        const int64_t blocks = (total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024;
+        k_check_finite<<<(unsigned)blocks, 256, 0, stream>>>(p.bands, A->n, A->kl, A->ku,
+                                                              reinterpret_cast<int *>(ws + L.flags));
+        if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+    }
+    if (n_pts == 0) return PSA_OK;
     if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
     return PSA_OK;
 }

@@ -37,7 +37,12 @@ struct KParams {
     // Lanczos controls
     int k_min, k_max;
     double tol;
-    // outputs (flat grid index)
+    // gradient kernel: explicit points z (zpts), upstream weights, outputs by point
+    const double2 *zpts;
+    const double *gweight;
+    double2 *grad_z;
+    double2 *grad_bands;
+    // outputs (flat grid index; point index for the gradient kernel)
     double *sigma;
     uint32_t *mask;
     int8_t *status;
@@ -49,6 +54,7 @@ struct KParams {
     char *wdata;        // per-warp blocks of warp_bytes, row records of row_bytes
     int64_t warp_bytes;
     int row_bytes;
+    int piv_offset;     // byte offset of the pivot bytes inside a row record
     int64_t P;          // threads launched (a multiple of kThreads)
 };
 
@@ -57,11 +63,17 @@ struct KernelOps {
     cudaError_t (*blocks_per_sm)(int *);  // resident blocks of kThreads per SM
 };
 
-// One entry per compiled (kl, ku); defined in psa_inst_kl*.cu.
+// One entry per compiled (kl, ku); defined in psa_inst_kl*.cu (sigma_min) and
+// psa_grad_kl*.cu (sigma_min with gradients).
 KernelOps kernel_ops_kl0(int ku);
 KernelOps kernel_ops_kl1(int ku);
 KernelOps kernel_ops_kl2(int ku);
 KernelOps kernel_ops_kl3(int ku);
 KernelOps kernel_ops_kl4(int ku);
+KernelOps grad_ops_kl0(int ku);
+KernelOps grad_ops_kl1(int ku);
+KernelOps grad_ops_kl2(int ku);
+KernelOps grad_ops_kl3(int ku);
+KernelOps grad_ops_kl4(int ku);
 
 }  // namespace psa

@@ -220,10 +220,415 @@ struct Shape {
     static constexpr int KW = KL + KU;         // superdiagonals of U after fill-in
     static constexpr int S = 2 * KL + KU + 1;  // factor values per row
     static constexpr int FA = S, FB = S + 1, FX = S + 2;
-    static constexpr int PIV = (S + 3) * 512;
+    static constexpr int FY = S + 3;  // gradient kernel only: the Ritz vector
     // 12 warps per SM while the elimination window is small, else 8
     static constexpr int MIN_BLOCKS = ((KL + 1) * (KW + 1) <= 24) ? 3 : 2;
 };
+
+// Lanczos scalars carried from step to step (see the kernel's header comment).
+struct LzState {
+    double acoef = 0.0;    // v_k = w_{k-1} - acoef v_{k-1}
+    double beta_p = 0.0;   // beta_{k-1}
+    double beta_pp = 0.0;  // beta_{k-2}
+    int e1 = 0;            // binary exponent of the largest component of B^{-1} q_1
+};
+
+// One Lanczos step k on the point held by this lane: sweeps (a), (b), (d), (e).
+// Returns -1 to go on, or the point's final status when the step ends the process
+// (0: beta_{k-1} = 0, the Krylov space is exhausted and theta_{k-1} is exact; 5: a
+// value left the double range). On return `alpha` holds alpha_k, beta_{k-1}^2 is in
+// Tb and alpha_k in Ta. With ACC, sweep (a) also adds yc * v_k into the field FY (the
+// Ritz vector of the gradient kernel); with only_a the step stops after sweep (a).
+template <int KL, int KU, bool ACC>
+__device__ __forceinline__ int lanczos_step(const KParams &p, char *const rows, uint8_t *const pivs, double *const Ta,
+                                            double *const Tb, const int k, LzState &st, double &alpha, const double yc,
+                                            const bool only_a)
+{
+    using SH = Shape<KL, KU>;
+    constexpr int KW = SH::KW;
+    constexpr int FA = SH::FA, FB = SH::FB, FX = SH::FX;
+    constexpr int64_t TS = 32;
+    const int n = p.n;
+    const int RB = p.row_bytes;
+#define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
+#define PIVOF(j) (pivs[(j) * RB])
+    const bool first = (k == 1);
+    const int fcur = (k & 1) ? FA : FB;   // v_k and, after (e), ...
+    const int fprv = (k & 1) ? FB : FA;   // v_{k-1}, replaced by w_k in (e)
+    // (a) v_k = w_{k-1} - st.acoef v_{k-1} (q_1 at k = 1); |v_k|^2; interchanges + L forward
+    double b2 = 0.0;
+    {
+        double2 X[KL + 1];
+        auto make_v = [&](int ii, double2 w, double2 vp) -> double2 {
+            const double2 v = first ? w : make_double2(fma(-st.acoef, vp.x, w.x), fma(-st.acoef, vp.y, w.y));
+            b2 = fma(v.x, v.x, fma(v.y, v.y, b2));
+            FLD(ii, fcur) = v;
+            if (ACC) {  // Ritz vector: y += yc v_k
+                const double2 y = first ? make_double2(0.0, 0.0) : FLD(ii, SH::FY);
+                FLD(ii, SH::FY) = make_double2(fma(yc, v.x, y.x), fma(yc, v.y, y.y));
+            }
+            return v;
+        };
+        auto load_w = [&](int ii, double2 &w, double2 &vp) {
+            if (first) { w = __ldg(&p.q1[ii]); vp = make_double2(0.0, 0.0); }
+            else { w = FLD(ii, fcur); vp = FLD(ii, fprv); }
+        };
+#pragma unroll
+        for (int r = 0; r < KL; ++r) {
+            X[r] = make_double2(0.0, 0.0);
+            if (r < n) { double2 w, vp; load_w(r, w, vp); X[r] = make_v(r, w, vp); }
+        }
+        // row j needs pivot j, multipliers of column j and v_{j+KL}; prefetch row j+1
+        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
+        int npv = 0;
+        auto load_a = [&](int j) {
+            if (KL > 0) {
+                npv = PIVOF(j);
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
+            }
+            if (j + KL < n) load_w(j + KL, nw, nvp);
+        };
+        load_a(0);
+        for (int j = 0; j < n; ++j) {
+            double2 cl[KL + 1];
+#pragma unroll
+            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
+            const int cpv = npv;
+            const double2 cw = nw, cvp = nvp;
+            if (j + 1 < n) load_a(j + 1);
+            X[KL] = (j + KL < n) ? make_v(j + KL, cw, cvp) : make_double2(0.0, 0.0);
+            if (KL > 0) {
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) {
+                    const bool s = (cpv == r);
+                    const double2 a = X[0], b = X[r];
+                    X[0] = s ? b : a;
+                    X[r] = s ? a : b;
+                }
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) X[r] = c_sub_mul(X[r], cl[r], X[0]);
+            }
+            FLD(j, FX) = X[0];
+#pragma unroll
+            for (int r = 0; r < KL; ++r) X[r] = X[r + 1];
+        }
+    }
+    if (only_a) return -1;
+    double invb = 1.0;
+    if (!first) {
+        if (b2 == 0.0) return 0;  // Krylov space exhausted: theta_{k-1} exact
+        if (!(b2 <= 1.7e308)) return 5;  // overflow: sigma below range
+        Tb[(int64_t)(k - 2) * TS] = b2;  // beta_{k-1}^2 = |v_k|^2 completes T_{k-1}
+        st.beta_pp = st.beta_p;
+        st.beta_p = sqrt(b2);
+        invb = 1.0 / st.beta_p;
+    }
+
+    // (b) U x = Vx backward; x_j = (Vx_j - sum U_{j,j+c} x_{j+c}) / U_jj
+    int emax = 0;
+    {
+        double2 Y[KW + 1];
+#pragma unroll
+        for (int c = 0; c <= KW; ++c) Y[c] = make_double2(0.0, 0.0);
+        double2 nu[KW + 1], nv;
+        auto load_b = [&](int j) {
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) nu[c] = FLD(j, c);
+            nv = FLD(j, FX);
+        };
+        load_b(n - 1);
+        for (int j = n - 1; j >= 0; --j) {
+            double2 cu[KW + 1];
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
+            double2 acc = nv;
+            if (j > 0) load_b(j - 1);
+#pragma unroll
+            for (int c = 1; c <= KW; ++c) acc = c_sub_mul(acc, cu[c], Y[c]);
+            const double2 x = c_mul(acc, cu[0]);
+            emax = max(emax, max(exp_field(x.x), exp_field(x.y)));
+            FLD(j, FX) = x;
+#pragma unroll
+            for (int c = KW; c >= 2; --c) Y[c] = Y[c - 1];
+            if (KW >= 1) Y[1] = x;
+        }
+    }
+    if (emax >= 2047) return 5;
+    // x is rescaled by 2^-es at the first step (fixing st.e1), at every step of
+    // a point with |st.e1| > 450, and at any step whose y (about x 2^st.e1) could
+    // come near the top of the double range. The decision is taken per warp;
+    // an exact power-of-two scale leaves every lane's result unchanged.
+    const bool scaled = __any_sync(__activemask(), first || st.e1 > 450 || st.e1 < -450 ||
+                                                       (emax - 1023) + st.e1 + 24 > 1000);
+    const int es = scaled ? clampi(emax - 1023, -1000, 1000) : 0;
+    if (first) st.e1 = es;
+    const double sc = pow2i(-es);
+
+    // (d) U^* t = x * 2^-es forward, accumulators for rows i..i+KW
+    {
+        double2 Acc[KW + 1];
+#pragma unroll
+        for (int c = 0; c < KW; ++c) {
+            double2 v = make_double2(0.0, 0.0);
+            if (c < n) { v = FLD(c, FX); if (scaled) { v.x *= sc; v.y *= sc; } }
+            Acc[c] = v;
+        }
+        double2 nu[KW + 1], nv = make_double2(0.0, 0.0);
+        auto load_d = [&](int i) {
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) nu[c] = FLD(i, c);
+            nv = (i + KW < n) ? FLD(i + KW, FX) : make_double2(0.0, 0.0);
+        };
+        load_d(0);
+        for (int i = 0; i < n; ++i) {
+            double2 cu[KW + 1];
+#pragma unroll
+            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
+            Acc[KW] = scaled ? make_double2(nv.x * sc, nv.y * sc) : nv;
+            if (i + 1 < n) load_d(i + 1);
+            const double2 tt = c_mul_conj(Acc[0], cu[0]);
+            FLD(i, FX) = tt;
+#pragma unroll
+            for (int c = 1; c <= KW; ++c) Acc[c] = c_sub_conjmul(Acc[c], cu[c], tt);
+#pragma unroll
+            for (int c = 0; c < KW; ++c) Acc[c] = Acc[c + 1];
+        }
+    }
+
+    // (e) L^* backward with interchanges; as each y_i becomes final,
+    //     w_i = F y_i - G v_{k-1,i} (= (H' q_k - beta_{k-1} q_{k-1})_i)
+    //     and asum += Re(conj(v_{k,i}) w_i)
+    const double F = scale2(first ? 1.0 : invb, es - 2 * st.e1);
+    const double G = (k == 2) ? st.beta_p : st.beta_p / (st.beta_pp > 0.0 ? st.beta_pp : 1.0);
+    double asum = 0.0;
+    {
+        auto emit = [&](int ii, double2 y, double2 vc, double2 vp) {
+            const double2 w = first ? make_double2(F * y.x, F * y.y)
+                                    : make_double2(fma(F, y.x, -(G * vp.x)), fma(F, y.y, -(G * vp.y)));
+            asum = fma(vc.x, w.x, fma(vc.y, w.y, asum));
+            FLD(ii, fprv) = w;
+        };
+        double2 T[KL + 1];
+#pragma unroll
+        for (int r = 0; r <= KL; ++r) T[r] = make_double2(0.0, 0.0);
+        // row j needs t_j, multipliers of column j, pivot j and v_k, v_{k-1} at j + KL
+        double2 nl[KL + 1], nt, nvc = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
+        int npv = 0;
+        auto load_e = [&](int j) {
+            nt = FLD(j, FX);
+            if (KL > 0) {
+                npv = PIVOF(j);
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
+            }
+            if (j + KL < n) {
+                nvc = FLD(j + KL, fcur);
+                nvp = first ? make_double2(0.0, 0.0) : FLD(j + KL, fprv);
+            }
+        };
+        load_e(n - 1);
+        for (int j = n - 1; j >= 0; --j) {
+            double2 cl[KL + 1];
+#pragma unroll
+            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
+            const int cpv = npv;
+            const double2 ct = nt, cvc = nvc, cvp = nvp;
+            if (j > 0) load_e(j - 1);
+#pragma unroll
+            for (int r = KL; r >= 1; --r) T[r] = T[r - 1];
+            T[0] = ct;
+            if (KL > 0) {
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) T[0] = c_sub_conjmul(T[0], cl[r], T[r]);
+#pragma unroll
+                for (int r = 1; r <= KL; ++r) {
+                    const bool s = (cpv == r);
+                    const double2 a = T[0], b = T[r];
+                    T[0] = s ? b : a;
+                    T[r] = s ? a : b;
+                }
+                if (j + KL < n) emit(j + KL, T[KL], cvc, cvp);
+            } else {
+                emit(j, T[0], cvc, cvp);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < KL; ++r)
+            if (r < n) emit(r, T[r], FLD(r, fcur), first ? make_double2(0.0, 0.0) : FLD(r, fprv));
+    }
+    // alpha_k = Re<q_k, w_k> = asum / beta_{k-1} (asum at k = 1, v_1 = q_1);
+    // v_{k+1} = w_k - alpha_k q_k = w_k - (alpha_k / beta_{k-1}) v_k
+    alpha = first ? asum : asum * invb;
+    st.acoef = first ? alpha : alpha * invb;
+    Ta[(int64_t)(k - 1) * TS] = alpha;
+    return -1;
+#undef FLD
+#undef PIVOF
+}
+
+// Banded LU of B = zI - A with partial pivoting inside the band, for the point z
+// held by this lane (all 32 lanes of the warp call it together; lanes without a
+// point pass a dummy z). A's diagonals for rows R0 .. R0+31 are staged in this
+// warp's shared-memory window Aw with one coalesced 512-byte load per diagonal:
+//   Aw[c][r - R0] = A[r][r + c - KL] = bands[c * n + r],  c = 0 .. KW.
+// The pivot of column j is the row of largest |Re| + |Im| among rows j .. j+KL (the
+// first on ties); U gains KL superdiagonals; the row record j keeps 1/U_jj, the
+// KW superdiagonal entries of U and the KL multipliers. Returns true when a column
+// had no nonzero pivot candidate (B singular).
+template <int KL, int KU>
+__device__ __forceinline__ bool band_lu(const KParams &p, char *const rows, uint8_t *const pivs, double2 (*const Aw)[32],
+                                        const int lane, const double zr, const double zi, const bool bad_input)
+{
+    using SH = Shape<KL, KU>;
+    constexpr int KW = SH::KW;
+    const int n = p.n;
+    const int RB = p.row_bytes;
+#define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
+#define PIVOF(j) (pivs[(j) * RB])
+int R0 = 0;
+auto stage = [&](int r0) {
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c <= KW; ++c) {
+        const int r = r0 + lane;
+        Aw[c][lane] = (r < n) ? __ldg(&p.bands[(int64_t)c * n + r]) : make_double2(0.0, 0.0);
+    }
+    __syncwarp();
+};
+if (!bad_input) stage(0);
+double2 W[KL + 1][KW + 1];
+#pragma unroll
+for (int r = 0; r <= KL; ++r)
+#pragma unroll
+    for (int c = 0; c <= KW; ++c) {
+        const int d = c - r;
+        double2 v = make_double2(0.0, 0.0);
+        if (!bad_input && d >= -KL && d <= KU && r < n && c < n) {
+            const double2 a = Aw[d + KL][r];
+            v = (d == 0) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+        }
+        W[r][c] = v;
+    }
+bool singular = false;
+for (int j = 0; j < (bad_input ? 0 : n); ++j) {
+    int pr = 0;
+    unsigned long long best = abs_bits(fabs(W[0][0].x) + fabs(W[0][0].y));
+#pragma unroll
+    for (int r = 1; r <= KL; ++r) {
+        const unsigned long long v = abs_bits(fabs(W[r][0].x) + fabs(W[r][0].y));
+        if (v > best) { best = v; pr = r; }
+    }
+#pragma unroll
+    for (int r = 1; r <= KL; ++r) {
+        const bool s = (pr == r);
+#pragma unroll
+        for (int c = 0; c <= KW; ++c) {
+            const double2 a = W[0][c], b = W[r][c];
+            W[0][c] = s ? b : a;
+            W[r][c] = s ? a : b;
+        }
+    }
+    // an exact zero pivot column: B is singular; the lane keeps stepping with a
+    // unit pivot (its factor is not used) so that the warp stays together
+    if (best == 0ULL) { singular = true; W[0][0] = make_double2(1.0, 0.0); }
+    const double2 rp = c_rcp(W[0][0]);
+    FLD(j, 0) = rp;
+#pragma unroll
+    for (int c = 1; c <= KW; ++c) FLD(j, c) = W[0][c];
+    if (KL > 0) PIVOF(j) = (uint8_t)pr;
+#pragma unroll
+    for (int r = 1; r <= KL; ++r) {
+        const double2 l = c_mul(W[r][0], rp);
+        FLD(j, KW + r) = l;
+#pragma unroll
+        for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < KL; ++r) {
+#pragma unroll
+        for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
+        W[r][KW] = make_double2(0.0, 0.0);
+    }
+    const int i = j + 1 + KL;  // next row, columns j+1 .. j+1+KW (d = c - KL)
+    if (i - R0 >= 32) { R0 += 32; stage(R0); }
+#pragma unroll
+    for (int c = 0; c <= KW; ++c) {
+        const int col = j + 1 + c;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < n && col < n) {
+            const double2 a = Aw[c][i - R0];
+            v = (c == KL) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
+        }
+        W[KL][c] = v;
+    }
+}
+
+    return singular;
+#undef FLD
+#undef PIVOF
+}
+
+// Lanczos on H' = (B B^*)^{-1} / 2^(2 e1) for the point held by this lane, after
+// band_lu: steps until the stopping test, beta = 0 or k_max. Returns the point's
+// status (0 OK, 2 NOT_CONVERGED, 5 UNDERFLOW) and sets sigma, the steps taken, the
+// final Ritz value theta (in H' units) and the Lanczos scalars st.
+template <int KL, int KU>
+__device__ __forceinline__ int lanczos_sigma(const KParams &p, char *const rows, uint8_t *const pivs, double *const Ta,
+                                             double *const Tb, LzState &st, double &sigma, int &ksteps, double &theta)
+{
+    constexpr int64_t TS = 32;
+    int status;
+    // ---------------- 2. Lanczos on H'
+    // The stored Lanczos vectors are v_k = u_k = beta_{k-1} q_k (v_1 = q_1), not
+    // normalised: 1/beta rides on the scalars of the next sweep. 2^e1 is the
+    // binary exponent of the largest component of B^{-1} q_1 (about 1/sigma);
+    // for |e1| <= 450 the solves of later steps stay inside the double range
+    // (x ~ beta 2^e1, y ~ beta 2^(2 e1) theta') and need no rescaling.
+    double theta_prev = 0.0, dprev = 0.0;
+    theta = 0.0;
+    sigma = 0.0;
+    ksteps = 0;
+    int kth = 0;  // step whose Ritz value `theta` holds
+    const int kmax = p.k_max;
+    const int kr0 = max(1, min(p.k_min, kmax) - 1);  // first step whose Ritz value is needed
+    const int kc0 = max(2, p.k_min);                 // first step with a stopping test
+    status = 2;  // NOT_CONVERGED
+    for (int k = 1;; ++k) {
+        double alpha = 0.0;
+        const int rs = lanczos_step<KL, KU, false>(p, rows, pivs, Ta, Tb, k, st, alpha, 0.0, false);
+        if (rs >= 0) { status = rs; break; }
+        ksteps = k;
+
+        // ---------------- 3. Ritz value and stopping test
+        if (k >= kr0) {
+            double th;
+            if (k == 1) th = alpha;
+            else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, st.beta_p * st.beta_p);
+            else th = ritz_top_cold(Ta, Tb, TS, k);
+            const bool have_prev = (kth == k - 1);
+            theta_prev = theta;
+            theta = th;
+            kth = k;
+            dprev = have_prev ? theta - theta_prev : 0.0;
+            if (k >= kc0 && have_prev && theta - theta_prev <= p.tol * theta) { status = 0; break; }
+        }
+        if (k >= kmax) break;
+    }
+    if (status != 5 && kth != ksteps && ksteps >= 1) {
+        theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, TS, ksteps);
+        kth = ksteps;
+    }
+    if (status != 5) {
+        if (!(theta > 0.0) || !(theta <= 1.7e308)) {
+            status = 5;
+        } else {
+            sigma = (1.0 / sqrt(theta)) * pow2i(clampi(-st.e1, -1022, 1023));
+        }
+    }
+    if (status == 5) sigma = 0.0;
+    return status;
+}
 
 // Flat grid index of lane `lane` of group g (-1: no point): on the full grid an
 // 8 x 4 tile (8 abscissae, 4 ordinates), whose neighbouring points take similar
@@ -262,7 +667,6 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
 {
     using SH = Shape<KL, KU>;
     constexpr int KW = SH::KW;
-    constexpr int FA = SH::FA, FB = SH::FB, FX = SH::FX;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n = p.n;
@@ -270,10 +674,9 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
     const int64_t ngrid = (int64_t)p.nx * p.ny;
     char *const wbase = p.wdata + warp * p.warp_bytes;
     char *const rows = wbase + lane * 16;
-    uint8_t *const pivs = reinterpret_cast<uint8_t *>(wbase) + SH::PIV + lane;
+    uint8_t *const pivs = reinterpret_cast<uint8_t *>(wbase) + p.piv_offset + lane;
     double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)n * RB) + lane;
     double *const Tb = Ta + (int64_t)p.k_max * 32;
-    constexpr int64_t TS = 32;  // stride of Ta / Tb in doubles
     const bool bad_input = p.flags[0] != 0;
     __shared__ double2 Aw_all[kThreads / 32][KW + 1][32];
     double2 (*const Aw)[32] = Aw_all[threadIdx.x >> 5];
@@ -315,343 +718,16 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
         }
 
         // ---------------- 1. banded LU with partial pivoting
-        // A's diagonals for rows R0 .. R0+31 sit in this warp's shared-memory window,
-        // loaded with one coalesced 512-byte access per diagonal:
-        //   Aw[c][r - R0] = A[r][r + c - KL] = bands[c * n + r],  c = 0 .. KW
-        int R0 = 0;
-        auto stage = [&](int r0) {
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c <= KW; ++c) {
-                const int r = r0 + lane;
-                Aw[c][lane] = (r < n) ? __ldg(&p.bands[(int64_t)c * n + r]) : make_double2(0.0, 0.0);
-            }
-            __syncwarp();
-        };
-        if (!bad_input) stage(0);
-        double2 W[KL + 1][KW + 1];
-#pragma unroll
-        for (int r = 0; r <= KL; ++r)
-#pragma unroll
-            for (int c = 0; c <= KW; ++c) {
-                const int d = c - r;
-                double2 v = make_double2(0.0, 0.0);
-                if (!bad_input && d >= -KL && d <= KU && r < n && c < n) {
-                    const double2 a = Aw[d + KL][r];
-                    v = (d == 0) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
-                }
-                W[r][c] = v;
-            }
-        bool singular = false;
-        for (int j = 0; j < (bad_input ? 0 : n); ++j) {
-            int pr = 0;
-            unsigned long long best = abs_bits(fabs(W[0][0].x) + fabs(W[0][0].y));
-#pragma unroll
-            for (int r = 1; r <= KL; ++r) {
-                const unsigned long long v = abs_bits(fabs(W[r][0].x) + fabs(W[r][0].y));
-                if (v > best) { best = v; pr = r; }
-            }
-#pragma unroll
-            for (int r = 1; r <= KL; ++r) {
-                const bool s = (pr == r);
-#pragma unroll
-                for (int c = 0; c <= KW; ++c) {
-                    const double2 a = W[0][c], b = W[r][c];
-                    W[0][c] = s ? b : a;
-                    W[r][c] = s ? a : b;
-                }
-            }
-            // an exact zero pivot column: B is singular; the lane keeps stepping with a
-            // unit pivot (its factor is not used) so that the warp stays together
-            if (best == 0ULL) { singular = true; W[0][0] = make_double2(1.0, 0.0); }
-            const double2 rp = c_rcp(W[0][0]);
-            FLD(j, 0) = rp;
-#pragma unroll
-            for (int c = 1; c <= KW; ++c) FLD(j, c) = W[0][c];
-            if (KL > 0) PIVOF(j) = (uint8_t)pr;
-#pragma unroll
-            for (int r = 1; r <= KL; ++r) {
-                const double2 l = c_mul(W[r][0], rp);
-                FLD(j, KW + r) = l;
-#pragma unroll
-                for (int c = 1; c <= KW; ++c) W[r][c] = c_sub_mul(W[r][c], l, W[0][c]);
-            }
-#pragma unroll
-            for (int r = 0; r < KL; ++r) {
-#pragma unroll
-                for (int c = 0; c < KW; ++c) W[r][c] = W[r + 1][c + 1];
-                W[r][KW] = make_double2(0.0, 0.0);
-            }
-            const int i = j + 1 + KL;  // next row, columns j+1 .. j+1+KW (d = c - KL)
-            if (i - R0 >= 32) { R0 += 32; stage(R0); }
-#pragma unroll
-            for (int c = 0; c <= KW; ++c) {
-                const int col = j + 1 + c;
-                double2 v = make_double2(0.0, 0.0);
-                if (i < n && col < n) {
-                    const double2 a = Aw[c][i - R0];
-                    v = (c == KL) ? make_double2(zr - a.x, zi - a.y) : make_double2(-a.x, -a.y);
-                }
-                W[KL][c] = v;
-            }
-        }
+        const bool singular = band_lu<KL, KU>(p, rows, pivs, Aw, lane, zr, zi, bad_input);
 
         if (have) {
             double sigma = 0.0;
             int status = bad_input ? 3 : 1;  // NONFINITE input, else SINGULAR
             int ksteps = 0;
             if (!singular && !bad_input) {
-                // ---------------- 2. Lanczos on H'
-                // The stored Lanczos vectors are v_k = u_k = beta_{k-1} q_k (v_1 = q_1), not
-                // normalised: 1/beta rides on the scalars of the next sweep. 2^e1 is the
-                // binary exponent of the largest component of B^{-1} q_1 (about 1/sigma);
-                // for |e1| <= 450 the solves of later steps stay inside the double range
-                // (x ~ beta 2^e1, y ~ beta 2^(2 e1) theta') and need no rescaling.
-                double theta = 0.0, theta_prev = 0.0, dprev = 0.0;
-                double acoef = 0.0;   // v_k = w_{k-1} - acoef * v_{k-1}
-                double beta_p = 0.0;  // beta_{k-1}
-                double beta_pp = 0.0; // beta_{k-2}
-                int e1 = 0;
-                int kth = 0;  // step whose Ritz value `theta` holds
-                const int kmax = p.k_max;
-                const int kr0 = max(1, min(p.k_min, kmax) - 1);  // first step whose Ritz value is needed
-                const int kc0 = max(2, p.k_min);                 // first step with a stopping test
-                status = 2;  // NOT_CONVERGED
-                for (int k = 1;; ++k) {
-                    const bool first = (k == 1);
-                    const int fcur = (k & 1) ? FA : FB;   // v_k and, after (e), ...
-                    const int fprv = (k & 1) ? FB : FA;   // v_{k-1}, replaced by w_k in (e)
-                    // (a) v_k = w_{k-1} - acoef v_{k-1} (q_1 at k = 1); |v_k|^2; interchanges + L forward
-                    double b2 = 0.0;
-                    {
-                        double2 X[KL + 1];
-                        auto make_v = [&](int ii, double2 w, double2 vp) -> double2 {
-                            const double2 v = first ? w : make_double2(fma(-acoef, vp.x, w.x), fma(-acoef, vp.y, w.y));
-                            b2 = fma(v.x, v.x, fma(v.y, v.y, b2));
-                            FLD(ii, fcur) = v;
-                            return v;
-                        };
-                        auto load_w = [&](int ii, double2 &w, double2 &vp) {
-                            if (first) { w = __ldg(&p.q1[ii]); vp = make_double2(0.0, 0.0); }
-                            else { w = FLD(ii, fcur); vp = FLD(ii, fprv); }
-                        };
-#pragma unroll
-                        for (int r = 0; r < KL; ++r) {
-                            X[r] = make_double2(0.0, 0.0);
-                            if (r < n) { double2 w, vp; load_w(r, w, vp); X[r] = make_v(r, w, vp); }
-                        }
-                        // row j needs pivot j, multipliers of column j and v_{j+KL}; prefetch row j+1
-                        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
-                        int npv = 0;
-                        auto load_a = [&](int j) {
-                            if (KL > 0) {
-                                npv = PIVOF(j);
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
-                            }
-                            if (j + KL < n) load_w(j + KL, nw, nvp);
-                        };
-                        load_a(0);
-                        for (int j = 0; j < n; ++j) {
-                            double2 cl[KL + 1];
-#pragma unroll
-                            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
-                            const int cpv = npv;
-                            const double2 cw = nw, cvp = nvp;
-                            if (j + 1 < n) load_a(j + 1);
-                            X[KL] = (j + KL < n) ? make_v(j + KL, cw, cvp) : make_double2(0.0, 0.0);
-                            if (KL > 0) {
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) {
-                                    const bool s = (cpv == r);
-                                    const double2 a = X[0], b = X[r];
-                                    X[0] = s ? b : a;
-                                    X[r] = s ? a : b;
-                                }
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) X[r] = c_sub_mul(X[r], cl[r], X[0]);
-                            }
-                            FLD(j, FX) = X[0];
-#pragma unroll
-                            for (int r = 0; r < KL; ++r) X[r] = X[r + 1];
-                        }
-                    }
-                    double invb = 1.0;
-                    if (!first) {
-                        if (b2 == 0.0) { status = 0; break; }  // Krylov space exhausted: theta exact
-                        if (!(b2 <= 1.7e308)) { status = 5; break; }  // overflow: sigma below range
-                        Tb[(int64_t)(k - 2) * TS] = b2;  // beta_{k-1}^2 = |v_k|^2 completes T_{k-1}
-                        beta_pp = beta_p;
-                        beta_p = sqrt(b2);
-                        invb = 1.0 / beta_p;
-                    }
-
-                    // (b) U x = Vx backward; x_j = (Vx_j - sum U_{j,j+c} x_{j+c}) / U_jj
-                    int emax = 0;
-                    {
-                        double2 Y[KW + 1];
-#pragma unroll
-                        for (int c = 0; c <= KW; ++c) Y[c] = make_double2(0.0, 0.0);
-                        double2 nu[KW + 1], nv;
-                        auto load_b = [&](int j) {
-#pragma unroll
-                            for (int c = 0; c <= KW; ++c) nu[c] = FLD(j, c);
-                            nv = FLD(j, FX);
-                        };
-                        load_b(n - 1);
-                        for (int j = n - 1; j >= 0; --j) {
-                            double2 cu[KW + 1];
-#pragma unroll
-                            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
-                            double2 acc = nv;
-                            if (j > 0) load_b(j - 1);
-#pragma unroll
-                            for (int c = 1; c <= KW; ++c) acc = c_sub_mul(acc, cu[c], Y[c]);
-                            const double2 x = c_mul(acc, cu[0]);
-                            emax = max(emax, max(exp_field(x.x), exp_field(x.y)));
-                            FLD(j, FX) = x;
-#pragma unroll
-                            for (int c = KW; c >= 2; --c) Y[c] = Y[c - 1];
-                            if (KW >= 1) Y[1] = x;
-                        }
-                    }
-                    if (emax >= 2047) { status = 5; break; }
-                    // x is rescaled by 2^-es at the first step (fixing e1), at every step of
-                    // a point with |e1| > 450, and at any step whose y (about x 2^e1) could
-                    // come near the top of the double range. The decision is taken per warp;
-                    // an exact power-of-two scale leaves every lane's result unchanged.
-                    const bool scaled = __any_sync(__activemask(), first || e1 > 450 || e1 < -450 ||
-                                                                       (emax - 1023) + e1 + 24 > 1000);
-                    const int es = scaled ? clampi(emax - 1023, -1000, 1000) : 0;
-                    if (first) e1 = es;
-                    const double sc = pow2i(-es);
-
-                    // (d) U^* t = x * 2^-es forward, accumulators for rows i..i+KW
-                    {
-                        double2 Acc[KW + 1];
-#pragma unroll
-                        for (int c = 0; c < KW; ++c) {
-                            double2 v = make_double2(0.0, 0.0);
-                            if (c < n) { v = FLD(c, FX); if (scaled) { v.x *= sc; v.y *= sc; } }
-                            Acc[c] = v;
-                        }
-                        double2 nu[KW + 1], nv = make_double2(0.0, 0.0);
-                        auto load_d = [&](int i) {
-#pragma unroll
-                            for (int c = 0; c <= KW; ++c) nu[c] = FLD(i, c);
-                            nv = (i + KW < n) ? FLD(i + KW, FX) : make_double2(0.0, 0.0);
-                        };
-                        load_d(0);
-                        for (int i = 0; i < n; ++i) {
-                            double2 cu[KW + 1];
-#pragma unroll
-                            for (int c = 0; c <= KW; ++c) cu[c] = nu[c];
-                            Acc[KW] = scaled ? make_double2(nv.x * sc, nv.y * sc) : nv;
-                            if (i + 1 < n) load_d(i + 1);
-                            const double2 tt = c_mul_conj(Acc[0], cu[0]);
-                            FLD(i, FX) = tt;
-#pragma unroll
-                            for (int c = 1; c <= KW; ++c) Acc[c] = c_sub_conjmul(Acc[c], cu[c], tt);
-#pragma unroll
-                            for (int c = 0; c < KW; ++c) Acc[c] = Acc[c + 1];
-                        }
-                    }
-
-                    // (e) L^* backward with interchanges; as each y_i becomes final,
-                    //     w_i = F y_i - G v_{k-1,i} (= (H' q_k - beta_{k-1} q_{k-1})_i)
-                    //     and asum += Re(conj(v_{k,i}) w_i)
-                    const double F = scale2(first ? 1.0 : invb, es - 2 * e1);
-                    const double G = (k == 2) ? beta_p : beta_p / (beta_pp > 0.0 ? beta_pp : 1.0);
-                    double asum = 0.0;
-                    {
-                        auto emit = [&](int ii, double2 y, double2 vc, double2 vp) {
-                            const double2 w = first ? make_double2(F * y.x, F * y.y)
-                                                    : make_double2(fma(F, y.x, -(G * vp.x)), fma(F, y.y, -(G * vp.y)));
-                            asum = fma(vc.x, w.x, fma(vc.y, w.y, asum));
-                            FLD(ii, fprv) = w;
-                        };
-                        double2 T[KL + 1];
-#pragma unroll
-                        for (int r = 0; r <= KL; ++r) T[r] = make_double2(0.0, 0.0);
-                        // row j needs t_j, multipliers of column j, pivot j and v_k, v_{k-1} at j + KL
-                        double2 nl[KL + 1], nt, nvc = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
-                        int npv = 0;
-                        auto load_e = [&](int j) {
-                            nt = FLD(j, FX);
-                            if (KL > 0) {
-                                npv = PIVOF(j);
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
-                            }
-                            if (j + KL < n) {
-                                nvc = FLD(j + KL, fcur);
-                                nvp = first ? make_double2(0.0, 0.0) : FLD(j + KL, fprv);
-                            }
-                        };
-                        load_e(n - 1);
-                        for (int j = n - 1; j >= 0; --j) {
-                            double2 cl[KL + 1];
-#pragma unroll
-                            for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
-                            const int cpv = npv;
-                            const double2 ct = nt, cvc = nvc, cvp = nvp;
-                            if (j > 0) load_e(j - 1);
-#pragma unroll
-                            for (int r = KL; r >= 1; --r) T[r] = T[r - 1];
-                            T[0] = ct;
-                            if (KL > 0) {
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) T[0] = c_sub_conjmul(T[0], cl[r], T[r]);
-#pragma unroll
-                                for (int r = 1; r <= KL; ++r) {
-                                    const bool s = (cpv == r);
-                                    const double2 a = T[0], b = T[r];
-                                    T[0] = s ? b : a;
-                                    T[r] = s ? a : b;
-                                }
-                                if (j + KL < n) emit(j + KL, T[KL], cvc, cvp);
-                            } else {
-                                emit(j, T[0], cvc, cvp);
-                            }
-                        }
-#pragma unroll
-                        for (int r = 0; r < KL; ++r)
-                            if (r < n) emit(r, T[r], FLD(r, fcur), first ? make_double2(0.0, 0.0) : FLD(r, fprv));
-                    }
-                    // alpha_k = Re<q_k, w_k> = asum / beta_{k-1} (asum at k = 1, v_1 = q_1);
-                    // v_{k+1} = w_k - alpha_k q_k = w_k - (alpha_k / beta_{k-1}) v_k
-                    const double alpha = first ? asum : asum * invb;
-                    acoef = first ? alpha : alpha * invb;
-                    Ta[(int64_t)(k - 1) * TS] = alpha;
-                    ksteps = k;
-
-                    // ---------------- 3. Ritz value and stopping test
-                    if (k >= kr0) {
-                        double th;
-                        if (k == 1) th = alpha;
-                        else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, beta_p * beta_p);
-                        else th = ritz_top_cold(Ta, Tb, TS, k);
-                        const bool have_prev = (kth == k - 1);
-                        theta_prev = theta;
-                        theta = th;
-                        kth = k;
-                        dprev = have_prev ? theta - theta_prev : 0.0;
-                        if (k >= kc0 && have_prev && theta - theta_prev <= p.tol * theta) { status = 0; break; }
-                    }
-                    if (k >= kmax) break;
-                }
-                if (status != 5 && kth != ksteps && ksteps >= 1) {
-                    theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, TS, ksteps);
-                    kth = ksteps;
-                }
-                if (status != 5) {
-                    if (!(theta > 0.0) || !(theta <= 1.7e308)) {
-                        status = 5;
-                    } else {
-                        sigma = (1.0 / sqrt(theta)) * pow2i(clampi(-e1, -1022, 1023));
-                    }
-                }
-                if (status == 5) sigma = 0.0;
+                LzState st;
+                double theta = 0.0;
+                status = lanczos_sigma<KL, KU>(p, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
             }
 
             // ---------------- 4. outputs

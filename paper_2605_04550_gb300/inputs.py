@@ -213,6 +213,15 @@ def jordan_block(n: int = 32):
     return _zero_outside(bands, n, 1, 0), 1, 0
 
 
+def grcar_perturbed(n: int, seed: int, scale: float = 1e-2):
+    """Grcar-type band (kl = 1, ku = 3) with every band entry perturbed by seeded
+    real Gaussian noise of standard deviation `scale`."""
+    b, kl, ku = grcar(n)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = b + scale * rng.standard_normal(b.shape)
+    return _zero_outside(b.astype(np.complex128), n, kl, ku), kl, ku
+
+
 def grcar_grid_100() -> Grid:
     """100 x 100 grid over Re z in [-1, 3], Im z in [-3.5, 3.5]."""
     return Grid(-1.0, 3.0, -3.5, 3.5, 100, 100)

@@ -356,3 +356,39 @@ def test_fixed_step_mode_runs_exactly_k_steps():
     _, st, k = oracle.sigma_min_banded(b, kl, ku, z, k_min=20, k_max=20)
     assert np.all(k == 20)
     assert np.all((st == oracle.OK) | (st == oracle.NOT_CONVERGED))
+
+
+# --------------------------------------------------------- gradient oracle
+def _fd_sigma(A, z, h=1e-6):
+    s = lambda zz: oracle.sigma_min_dense(A, [zz])[0]
+    return complex((s(z + h) - s(z - h)) / (2 * h), (s(z + 1j * h) - s(z - 1j * h)) / (2 * h))
+
+
+@pytest.mark.parametrize("case", ["grcar", "toeplitz", "paper"])
+def test_gradient_formula_matches_finite_differences(case):
+    if case == "grcar":
+        b, kl, ku = inputs.grcar(40)
+        zs = [1.5 + 2.5j, 0.3 - 1.7j]
+    elif case == "toeplitz":
+        b, kl, ku, _ = inputs.random_toeplitz(30, 2, 5, seed=1)
+        zs = [6.0 + 4.0j, -3.0 + 1.0j]
+    else:
+        b, kl, ku, _ = inputs.paper_class(2)
+        zs = [2.5 + 1.5j, -3.0 - 2.0j]
+    A = oracle.band_to_dense(b, kl, ku)
+    for z in zs:
+        s, gz, gA = oracle.sigma_min_grad_dense(A, z)
+        fd = _fd_sigma(A, z)
+        assert abs(gz - fd) <= 1e-6 * abs(fd) + 1e-9, (z, gz, fd)
+        # one band entry, real and imaginary directions
+        i, d = 7, 1
+        E = np.zeros_like(A)
+        E[i, i + d] = 1.0
+        h = 1e-6
+        sp = oracle.sigma_min_dense(A + h * E, [z])[0]
+        sm = oracle.sigma_min_dense(A - h * E, [z])[0]
+        spi = oracle.sigma_min_dense(A + 1j * h * E, [z])[0]
+        smi = oracle.sigma_min_dense(A - 1j * h * E, [z])[0]
+        fda = complex((sp - sm) / (2 * h), (spi - smi) / (2 * h))
+        gb = oracle.dense_grad_to_bands(gA, kl, ku)
+        assert abs(gb[d + kl, i] - fda) <= 1e-6 * abs(fda) + 1e-9, (gb[d + kl, i], fda)
