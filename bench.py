@@ -368,6 +368,71 @@ def run_gpu(args):
     return 0
 
 
+def run_differentiation(args):
+    """Adjoint workload: Grcar-type n = 4000 (kl = 1, ku = 3) with N(0, 1e-2) band noise;
+    ~1e5 grid points with d sigma / dz and the band gradient (unit weights), a
+    central-difference check (h = 1e-6) at sampled points, and Newton refinement of
+    the eps = 1e-4 contour along grid rows."""
+    import torch
+    import paper_2605_04550_gb300 as psa
+    from paper_2605_04550_gb300 import contour
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    b, kl, ku = inputs.grcar_perturbed(4000, seed=0)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 320, 313)
+    bt = torch.as_tensor(b, device=dev)
+    xs = grid.re_min + np.arange(grid.nx) * ((grid.re_max - grid.re_min) / (grid.nx - 1))
+    ys = grid.im_min + np.arange(grid.ny) * ((grid.im_max - grid.im_min) / (grid.ny - 1))
+    z = torch.as_tensor((xs[None, :] + 1j * ys[:, None]).ravel(), device=dev)
+    w = torch.ones(z.numel(), dtype=torch.float64, device=dev)
+    opts = psa.LanczosOpts()
+    for _ in range(args.warmup):
+        r = psa.sigma_min_grad(bt, kl, ku, z, weight=w, opts=opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        r = psa.sigma_min_grad(bt, kl, ku, z, weight=w, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    sig = r.sigma.cpu().numpy()
+    st = r.status.cpu().numpy()
+    steps = r.steps.cpu().numpy()
+    # central differences at resolvable sampled points
+    rng = np.random.default_rng(0)
+    cand = np.flatnonzero(sig > 1e-3)
+    pick = rng.choice(cand, min(64, cand.size), replace=False)
+    zc = z.cpu().numpy()[pick]
+    h = 1e-6
+    tight = psa.LanczosOpts(tol=1e-15, k_max=4000)
+    zz = torch.as_tensor(np.concatenate([zc, zc + h, zc - h, zc + 1j * h, zc - 1j * h]), device=dev)
+    rf = psa.sigma_min_grad(bt, kl, ku, zz, opts=tight)
+    sf = rf.sigma.cpu().numpy().reshape(5, -1)
+    fd = (sf[1] - sf[2]) / (2 * h) + 1j * (sf[3] - sf[4]) / (2 * h)
+    gz = rf.grad_z.cpu().numpy()[: pick.size]
+    fd_err = float(np.max(np.abs(gz - fd) / np.abs(fd)))
+    # Newton refinement of the eps = 1e-4 contour along grid rows
+    t0 = time.perf_counter()
+    ref = contour.refine_rows(bt, kl, ku, grid, sig.reshape(grid.ny, grid.nx), 1e-4)
+    newton_s = time.perf_counter() - t0
+    npts = z.numel()
+    line = {"workload": "differentiation", "metric": "sigma_min + adjoint gradient points/s (FP64)",
+            "value": npts / (ms * 1e-3), "unit": "grid points/s", "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Grcar-type n=4000 kl=1 ku=3, band entries + N(0,1e-2) (seed 0), "
+                                   f"{grid.nx}x{grid.ny} grid over [-1,3]x[-3.5,3.5], grad_z and band gradient "
+                                   "(unit weights), Lanczos tol 1e-13"},
+            "mean_lanczos_steps": float(steps.mean()),
+            "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+            "fd_check": {"points": int(pick.size), "h": h, "max_rel_err": fd_err},
+            "newton_contour": {"eps": 1e-4, "crossings": int(ref.x.size), "converged": int(ref.converged.sum()),
+                               "gpu_calls": ref.iterations, "max_rel_residual": float(ref.residual.max()),
+                               "seconds": newton_s}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,10 +443,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--case", default="mid", choices=["mid", "small"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures")
+    ap.add_argument("--workload", default="grid", choices=["grid", "differentiation"],
+                    help="grid: the benchmark line; differentiation: the adjoint workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "differentiation":
+        return run_differentiation(args)
     return run_gpu(args)
 
 
