@@ -110,7 +110,7 @@ psa_lanczos_opts psa_default_opts(void);
  * `points_in_flight` points in flight at once (rounded up to whole warps of
  * 32), for calls of up to `npoints` points (grid points, or list entries in
  * restricted mode). The workspace holds a 256-byte flag block; the work-order
- * schedule (8 KB plus 8 bytes per group of 32 points, at most npoints / 8 + 2
+ * schedule (32 KB plus 8 bytes per group of 32 points, at most npoints / 8 + 2
  * groups); the shared start vector (n complex values); and one block per
  * warp: for each of the n rows the warp's pivoted band factor (2kl + ku + 1
  * complex values per point), three Lanczos vectors and the pivot offsets, then
@@ -240,6 +240,98 @@ int psa_sigma_min_static(const psa_band *A, const psa_grid *g,
                          const int32_t *idx, int64_t n_idx,
                          double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
                          const psa_lanczos_opts *opts, void *stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent matrices, each with its own grid, in one call. The paper
+ * evaluates one matrix at a time; a batch serves the same per-point quantity
+ * to callers with many small or mid-size problems (a parameter sweep, a
+ * family of discretisations), where one grid alone cannot fill the device.
+ * Results are bit-identical to psa_sigma_min on each matrix alone with the
+ * same opts: every point is computed by the same arithmetic from the same
+ * start vector; only the order in which warps take the points differs. */
+
+/* One matrix of a batch: its band (DEVICE bands pointer), its full grid, and
+ * where its results start in the batch outputs: point (i, j) of the grid goes
+ * to sigma[out_offset + i * g.nx + j] (likewise mask, status, steps). The
+ * caller keeps the output ranges of different entries disjoint. */
+typedef struct {
+    psa_band A;
+    psa_grid g;
+    int64_t out_offset;
+} psa_batch_entry;
+
+/* Order of the groups (8 x 4 grid tiles) within one band-shape class. */
+#define PSA_BATCH_ORDER_AUTO 0      /* estimate pass when warps take >= 2 groups each */
+#define PSA_BATCH_ORDER_PLAN 1      /* plan order: matrices by decreasing n, tiles in grid order */
+#define PSA_BATCH_ORDER_ESTIMATE 2  /* always: anchor points, 4 Lanczos steps, longest first */
+
+/* Bytes of the plan of a batch of nmat matrices (host call). Errors: PSA_EINVAL
+ * (nmat < 0 or bytes == NULL). */
+int psa_batch_plan_bytes(int32_t nmat, size_t *bytes);
+
+/* Builds the plan of a batch in HOST memory `plan` (plan_bytes from
+ * psa_batch_plan_bytes): the matrices grouped into classes of equal (kl, ku),
+ * each class ordered by decreasing n, with the offsets of each matrix's tiles,
+ * start vector and outputs. The plan holds the entries' device bands pointers;
+ * the caller copies its bytes unchanged to device memory (256-byte aligned)
+ * before psa_sigma_min_batched and keeps both copies and the bands alive while
+ * calls that use them run. Host call, no device work.
+ * Errors: PSA_EINVAL (an entry with bad band or grid fields, a NULL bands
+ * pointer, out_offset < 0, a grid of more than 2^31 - 1 points, nmat < 0,
+ * plan NULL or plan_bytes too small), PSA_EUNSUPPORTED (kl > 4 or ku > 8, or
+ * a class of more than 2^31 - 1 groups). */
+int psa_batch_plan(const psa_batch_entry *entries, int32_t nmat, void *plan, size_t plan_bytes);
+
+/* Bytes of device workspace for psa_sigma_min_batched with up to
+ * `points_in_flight` points (whole warps) in flight in each class and
+ * `n_streams` (1 to 8) streams: a counter block, one flag per matrix, the start
+ * vectors of all matrices, then per stream the work-order schedule of the
+ * largest class and a region of warp blocks (per warp the block
+ * psa_workspace_bytes describes, for the largest n of the class) that the
+ * classes of that stream use one after another. Host call.
+ * Errors: PSA_EINVAL. */
+int psa_batch_workspace_bytes(const void *plan_host, const psa_lanczos_opts *opts, int64_t points_in_flight,
+                              int32_t n_streams, size_t *bytes);
+
+/* sigma_min on every grid point of every matrix of a batch, with the eps
+ * masks of psa_sigma_min. A set-up pass (all start vectors, input checks) on
+ * `stream`, then per band-shape class an optional estimate pass and one
+ * persistent sigma_min launch. With auxiliary streams the classes are split
+ * over `stream` and the n_aux streams `aux_streams` (longest estimated first,
+ * each class to the stream with the least estimated work so far; estimate =
+ * points x n x flops per Lanczos row-step): the launches of several classes
+ * are then in flight at once and the device's block scheduler fills the tail
+ * of one class with blocks of the others. The auxiliary streams wait for the
+ * set-up on `stream`, and `stream` waits for the last class of every auxiliary
+ * stream before the call returns (events of the library, created at the first
+ * call on a device). The call allocates no memory and copies nothing between
+ * host and device, so a whole batch can be captured in one CUDA graph and
+ * replayed (make one call outside capture first so that the events exist).
+ *  plan_host, plan_dev  the plan (psa_batch_plan) in host memory and its copy
+ *                   in device memory.
+ *  eps, n_eps       as psa_sigma_min (host array).
+ *  sigma, mask, status, steps  DEVICE outputs indexed by the entries'
+ *                   out_offset (mask, status, steps may be NULL).
+ *  opts             Lanczos controls (NULL = psa_default_opts()).
+ *  points_in_flight per class at most this many points in flight (0: as many
+ *                   as the workspace and one full occupancy of the device allow).
+ *  order            PSA_BATCH_ORDER_*.
+ *  workspace, ws_bytes  DEVICE scratch, 256-byte aligned
+ *                   (psa_batch_workspace_bytes with the same number of
+ *                   streams); each stream's region is (ws_bytes - fixed part)
+ *                   / streams, and a class runs as many warps as its region
+ *                   holds, up to the caps above.
+ *  stream           cudaStream_t of the call.
+ *  aux_streams, n_aux  0 to 7 further cudaStream_t, all different from each
+ *                   other and from stream (n_aux = 0: every class on stream).
+ * Errors: PSA_EINVAL (bad eps, opts or order, a plan whose header does not
+ * check, n_aux out of range, a repeated stream), PSA_EWORKSPACE (no room for
+ * one warp in some class), PSA_ECUDA. */
+int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const double *eps, int32_t n_eps,
+                          double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
+                          const psa_lanczos_opts *opts, int64_t points_in_flight, int32_t order,
+                          void *workspace, size_t ws_bytes, void *stream, void *const *aux_streams,
+                          int32_t n_aux);
 
 /* Measured FP64 throughput of this device: runs a kernel of independent DFMA
  * chains (iters iterations, 8 chains, SM count x 16 warps) on `stream`,

@@ -28,8 +28,14 @@ EXPORTS = (
     "psa_sigma_min_static",
     "psa_grad_workspace_bytes",
     "psa_sigma_min_grad",
+    "psa_batch_plan_bytes",
+    "psa_batch_plan",
+    "psa_batch_workspace_bytes",
+    "psa_sigma_min_batched",
     "psa_probe_dfma_rate",
 )
+
+BATCH_ORDER_AUTO, BATCH_ORDER_PLAN, BATCH_ORDER_ESTIMATE = 0, 1, 2
 
 
 class PsaBand(ctypes.Structure):
@@ -46,6 +52,10 @@ class PsaGrid(ctypes.Structure):
 class PsaLanczosOpts(ctypes.Structure):
     _fields_ = [("k_min", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class PsaBatchEntry(ctypes.Structure):
+    _fields_ = [("A", PsaBand), ("g", PsaGrid), ("out_offset", ctypes.c_int64)]
 
 
 class PsaError(RuntimeError):
@@ -95,6 +105,17 @@ def load(path: str | None = None):
         lib.psa_sigma_min_grad.restype = ctypes.c_int
         lib.psa_sigma_min_grad.argtypes = [ctypes.POINTER(PsaBand), vp, i64, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
+        lib.psa_batch_plan_bytes.restype = ctypes.c_int
+        lib.psa_batch_plan_bytes.argtypes = [i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_batch_plan.restype = ctypes.c_int
+        lib.psa_batch_plan.argtypes = [ctypes.POINTER(PsaBatchEntry), i32, vp, ctypes.c_size_t]
+        lib.psa_batch_workspace_bytes.restype = ctypes.c_int
+        lib.psa_batch_workspace_bytes.argtypes = [vp, ctypes.POINTER(PsaLanczosOpts), i64, i32,
+                                                  ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_sigma_min_batched.restype = ctypes.c_int
+        lib.psa_sigma_min_batched.argtypes = [vp, vp, ctypes.POINTER(dbl), i32, vp, vp, vp, vp,
+                                              ctypes.POINTER(PsaLanczosOpts), i64, i32, vp, ctypes.c_size_t, vp,
+                                              ctypes.POINTER(vp), i32]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         _lib = lib

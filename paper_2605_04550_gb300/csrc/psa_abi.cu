@@ -1,8 +1,11 @@
 // psa_abi.cu -- the C ABI of libpsa: argument checks, workspace layout,
 // set-up kernels and dispatch of the sigma_min kernel by band shape.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "psa.h"
@@ -80,8 +83,9 @@ __device__ __forceinline__ double unit_interval(unsigned long long v)
     return __ull2double_rn(v >> 11) * 0x1.0p-52 - 1.0;
 }
 
-// q1 = h / |h|, h_i = u(2i) + i u(2i+1): one block, fixed-order reduction.
-__global__ void __launch_bounds__(256) k_start_vector(double2 *q1, int n, unsigned long long seed)
+// q1 = h / |h|, h_i = u(2i) + i u(2i+1), by one block of 256 threads with a
+// fixed-order reduction (the same bits for a matrix alone and in a batch).
+__device__ __forceinline__ void start_vector_block(double2 *q1, int n, unsigned long long seed)
 {
     __shared__ double red[256];
     double s = 0.0;
@@ -104,6 +108,11 @@ __global__ void __launch_bounds__(256) k_start_vector(double2 *q1, int n, unsign
     }
 }
 
+__global__ void __launch_bounds__(256) k_start_vector(double2 *q1, int n, unsigned long long seed)
+{
+    start_vector_block(q1, n, seed);
+}
+
 // flags[0] |= 1 when a band entry A[i][i+d] (0 <= i+d < n) is not finite.
 __global__ void k_check_finite(const double2 *bands, int n, int kl, int ku, int *flags)
 {
@@ -118,17 +127,35 @@ __global__ void k_check_finite(const double2 *bands, int n, int kl, int ku, int 
     }
 }
 
-// cursor[b] = number of groups in buckets above b (descending order of buckets).
-__global__ void __launch_bounds__(1024) k_sched_scan(const int *hist, int *cursor)
+// cursor[b] = number of groups in buckets above b (descending order of buckets):
+// one block of 1024 threads, thread t owns buckets 4t .. 4t+3; an inclusive scan of
+// the per-thread sums from the top (Hillis-Steele in shared memory) gives each
+// thread the count above its buckets.
+constexpr int kScanThreads = 1024;
+static_assert(kBuckets == 4 * kScanThreads, "k_sched_scan: 4 buckets per thread");
+__global__ void __launch_bounds__(kScanThreads) k_sched_scan(const int *hist, int *cursor)
 {
-    __shared__ int h[kBuckets];
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = hist[b];
+    __shared__ int s[2][kScanThreads];
+    const int t = threadIdx.x;
+    const int4 h = reinterpret_cast<const int4 *>(hist)[t];
+    // thread index r = 1023 - t so that the scan runs from the highest buckets down
+    const int r = kScanThreads - 1 - t;
+    s[0][r] = h.x + h.y + h.z + h.w;
     __syncthreads();
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
-        int s = 0;
-        for (int c = b + 1; c < kBuckets; ++c) s += h[c];
-        cursor[b] = s;
+    int cur = 0;
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        const int v = s[cur][r] + (r >= off ? s[cur][r - off] : 0);
+        s[cur ^ 1][r] = v;
+        cur ^= 1;
+        __syncthreads();
     }
+    const int above = s[cur][r] - (h.x + h.y + h.z + h.w);  // buckets > 4t + 3
+    int4 c;
+    c.w = above;
+    c.z = c.w + h.w;
+    c.y = c.z + h.z;
+    c.x = c.y + h.y;
+    reinterpret_cast<int4 *>(cursor)[t] = c;
 }
 
 // order[slot] = group, groups of higher buckets first (order within a bucket is
@@ -151,6 +178,31 @@ __global__ void k_fill_not_evaluated(double *sigma, uint32_t *mask, int8_t *stat
         if (mask) mask[i] = 0u;
         if (status) status[i] = (int8_t)PSA_PT_NOT_EVALUATED;
         if (steps) steps[i] = 0;
+    }
+}
+
+// Batch start vectors, one block per matrix of the plan (as k_start_vector).
+__global__ void __launch_bounds__(256) k_batch_start_vectors(const PlanMat *mats, double2 *q1,
+                                                             unsigned long long seed)
+{
+    const PlanMat &e = mats[blockIdx.x];
+    start_vector_block(q1 + e.q1_off, e.n, seed);
+}
+
+// Batch input check of one class (band shape kl, ku): blockIdx.y = matrix within the
+// class, blocks in x stride over its band entries.
+__global__ void k_batch_check_finite(const PlanMat *mats, int kl, int ku, int *mflags)
+{
+    const PlanMat &e = mats[blockIdx.y];
+    const int n = e.n;
+    const int64_t total = (int64_t)(kl + ku + 1) * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int dk = (int)(q / n);
+        const int i = (int)(q - (int64_t)dk * n);
+        const int col = i + dk - kl;
+        if (col < 0 || col >= n) continue;
+        const double2 a = e.bands[q];
+        if (!isfinite(a.x) || !isfinite(a.y)) atomicOr(&mflags[blockIdx.y], 1);
     }
 }
 
@@ -326,6 +378,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.idx = idx;
     p.npts = npts;
     p.ngroups = ngroups;
+    p.nchunks = (ngroups + 31) / 32;
     for (int l = 0; l < kMaxEps; ++l) p.eps[l] = l < n_eps ? eps[l] : 0.0;
     p.n_eps = n_eps;
     p.k_min = o.k_min;
@@ -350,6 +403,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
     p.warp_bytes = L.warp_bytes;
     p.row_bytes = L.row_bytes;
     p.piv_offset = (2 * A->kl + A->ku + 1 + 3) * 512;
+    p.trow = A->n;
     p.P = P;
 
     if (mask && n_eps == 0) {
@@ -386,7 +440,7 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
         pe.status = nullptr;
         pe.steps = nullptr;
         if (ops.launch(pe, stream) != cudaSuccess) return PSA_ECUDA;
-        k_sched_scan<<<1, 1024, 0, stream>>>(hist, cursor);
+        k_sched_scan<<<1, kScanThreads, 0, stream>>>(hist, cursor);
         if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
         const int64_t sb = (ngroups + 255) / 256 < 4096 ? (ngroups + 255) / 256 : 4096;
         k_sched_scatter<<<(unsigned)sb, 256, 0, stream>>>(bucket, cursor, order, ngroups);
@@ -443,6 +497,7 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
     p.ny = 1;
     p.npts = n_pts;
     p.ngroups = ngroups;
+    p.nchunks = (ngroups + 31) / 32;
     p.k_min = o.k_min;
     p.k_max = o.k_max;
     p.tol = o.tol;
@@ -460,6 +515,7 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
     p.warp_bytes = L.warp_bytes;
     p.row_bytes = L.row_bytes;
     p.piv_offset = (2 * A->kl + A->ku + 1 + 4) * 512;
+    p.trow = A->n;
     p.P = nwarps * 32;
 
     if (grad_bands &&
@@ -477,6 +533,359 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
     }
     if (n_pts == 0) return PSA_OK;
     if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
+    return PSA_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+int psa_batch_plan_bytes(int32_t nmat, size_t *bytes)
+{
+    if (nmat < 0 || !bytes) return PSA_EINVAL;
+    *bytes = kPlanMatOff + align_up(sizeof(PlanMat) * (size_t)nmat);
+    return PSA_OK;
+}
+
+int psa_batch_plan(const psa_batch_entry *entries, int32_t nmat, void *plan, size_t plan_bytes)
+{
+    size_t need = 0;
+    if (psa_batch_plan_bytes(nmat, &need) != PSA_OK || !plan || plan_bytes < need || (nmat > 0 && !entries))
+        return PSA_EINVAL;
+    for (int32_t m = 0; m < nmat; ++m) {
+        const psa_batch_entry &e = entries[m];
+        const psa_grid &g = e.g;
+        if (!band_ok(&e.A) || !e.A.bands || e.out_offset < 0) return PSA_EINVAL;
+        if (!(std::isfinite(g.re_min) && std::isfinite(g.re_max) && std::isfinite(g.im_min) &&
+              std::isfinite(g.im_max)) ||
+            g.re_min > g.re_max || g.im_min > g.im_max || g.nx < 1 || g.ny < 1 ||
+            (int64_t)g.nx * g.ny > 2147483647LL)
+            return PSA_EINVAL;
+        if (e.A.kl > kMaxKL || e.A.ku > kMaxKU || !fits_row_offsets(&e.A)) return PSA_EUNSUPPORTED;
+    }
+    // matrices by class (kl, ku), within a class by decreasing n (stable)
+    std::vector<int32_t> ord((size_t)nmat);
+    for (int32_t m = 0; m < nmat; ++m) ord[(size_t)m] = m;
+    auto cls = [&](int32_t m) { return entries[m].A.kl * (kMaxKU + 1) + entries[m].A.ku; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        if (cls(a) != cls(b)) return cls(a) < cls(b);
+        return entries[a].A.n > entries[b].A.n;
+    });
+    char *const base = static_cast<char *>(plan);
+    std::memset(base, 0, need);
+    PlanHeader &H = *reinterpret_cast<PlanHeader *>(base);
+    PlanClass *const C = reinterpret_cast<PlanClass *>(base + kPlanClassOff);
+    PlanMat *const M = reinterpret_cast<PlanMat *>(base + kPlanMatOff);
+    int64_t q1 = 0;
+    int nclass = 0;
+    for (int32_t r = 0; r < nmat; ++r) {
+        const psa_batch_entry &e = entries[ord[(size_t)r]];
+        if (r == 0 || cls(ord[(size_t)r]) != cls(ord[(size_t)r - 1])) {
+            PlanClass &c = C[nclass++];
+            c.kl = e.A.kl;
+            c.ku = e.A.ku;
+            c.n_max = e.A.n;  // the class's first matrix is its largest
+            c.first = r;
+        }
+        PlanClass &c = C[nclass - 1];
+        PlanMat &pm = M[r];
+        pm.bands = reinterpret_cast<const double2 *>(e.A.bands);
+        pm.n = e.A.n;
+        pm.nx = e.g.nx;
+        pm.ny = e.g.ny;
+        pm.re_min = e.g.re_min;
+        pm.im_min = e.g.im_min;
+        pm.hx = e.g.nx > 1 ? (e.g.re_max - e.g.re_min) / (double)(e.g.nx - 1) : 0.0;
+        pm.hy = e.g.ny > 1 ? (e.g.im_max - e.g.im_min) / (double)(e.g.ny - 1) : 0.0;
+        pm.out_off = e.out_offset;
+        pm.q1_off = q1;
+        pm.gstart = c.ngroups;
+        pm.estart = c.nchunks;
+        const int64_t groups = (int64_t)((e.g.nx + 7) / 8) * ((e.g.ny + 3) / 4);
+        c.ngroups += groups;
+        c.nchunks += (groups + 31) / 32;
+        c.count += 1;
+        q1 += e.A.n;
+        if (c.ngroups > 2147483647LL) return PSA_EUNSUPPORTED;
+        if (e.A.n > H.max_n) H.max_n = e.A.n;
+    }
+    for (int c = 0; c < nclass; ++c)
+        if (C[c].ngroups > H.max_ngroups) H.max_ngroups = C[c].ngroups;
+    H.magic = kPlanMagic;
+    H.nmat = nmat;
+    H.nclass = nclass;
+    H.q1_total = q1;
+    return PSA_OK;
+}
+
+namespace {
+
+// Batch workspace: [class counters: 2 ints per class][mflags: one int per matrix]
+// [start vectors][per stream: schedule of the largest class][per stream: region of
+// warp blocks, used by the stream's classes one after another].
+struct BatchLayout {
+    size_t counters, mflags, q1, sched, regions;  // offsets
+    size_t sched_bytes;                             // one stream's schedule
+};
+
+BatchLayout batch_layout(const PlanHeader &H, int nstreams)
+{
+    BatchLayout B{};
+    size_t off = 0;
+    B.counters = off; off += align_up(sizeof(int) * 2 * (size_t)kMaxClasses);
+    B.mflags = off;   off += align_up(sizeof(int) * (size_t)(H.nmat > 0 ? H.nmat : 1));
+    B.q1 = off;       off += align_up(sizeof(double2) * (size_t)H.q1_total);
+    B.sched_bytes = sched_bytes(H.max_ngroups);
+    B.sched = off;    off += (size_t)nstreams * B.sched_bytes;
+    B.regions = off;
+    return B;
+}
+
+bool plan_ok(const void *plan_host)
+{
+    if (!plan_host) return false;
+    const PlanHeader &H = *static_cast<const PlanHeader *>(plan_host);
+    return H.magic == kPlanMagic && H.nmat >= 0 && H.nclass >= 0 && H.nclass <= kMaxClasses &&
+           (H.nmat == 0) == (H.nclass == 0);
+}
+
+const PlanClass *plan_classes(const void *plan_host)
+{
+    return reinterpret_cast<const PlanClass *>(static_cast<const char *>(plan_host) + kPlanClassOff);
+}
+
+// Estimated work of a class: sum over its matrices of points x n x flops per
+// Lanczos row-step (the step count is not known before the run).
+double class_cost(const void *plan_host, const PlanClass &c)
+{
+    const PlanMat *M = reinterpret_cast<const PlanMat *>(static_cast<const char *>(plan_host) + kPlanMatOff);
+    double w = 0.0;
+    for (int m = c.first; m < c.first + c.count; ++m)
+        w += (double)M[m].nx * (double)M[m].ny * (double)M[m].n;
+    return w * (16.0 * (2 * c.kl + c.ku) + 30.0);
+}
+
+// Classes in launch order (decreasing estimated work) and the stream of each:
+// every class goes to the stream with the least estimated work so far (first on ties).
+void stream_schedule(const void *plan_host, int nclass, int nstreams, int *order, int *lane)
+{
+    const PlanClass *C = plan_classes(plan_host);
+    double cost[kMaxClasses];
+    for (int c = 0; c < nclass; ++c) {
+        order[c] = c;
+        cost[c] = class_cost(plan_host, C[c]);
+    }
+    std::stable_sort(order, order + nclass, [&](int a, int b) { return cost[a] > cost[b]; });
+    double load[kMaxStreams] = {};
+    for (int r = 0; r < nclass; ++r) {
+        const int c = order[r];
+        int s = 0;
+        for (int t = 1; t < nstreams; ++t)
+            if (load[t] < load[s]) s = t;
+        lane[c] = s;
+        load[s] += cost[c];
+    }
+}
+
+// Events per device: [0] forks the auxiliary streams off the caller's stream,
+// [1 + k] joins auxiliary stream k back.
+constexpr int kMaxDevices = 64;
+std::mutex g_ev_mu;
+cudaEvent_t g_ev[kMaxDevices][kMaxStreams] = {};
+
+int batch_events(cudaEvent_t **ev)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSA_ECUDA;
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    for (int k = 0; k < kMaxStreams; ++k)
+        if (!g_ev[dev][k] && cudaEventCreateWithFlags(&g_ev[dev][k], cudaEventDisableTiming) != cudaSuccess) {
+            g_ev[dev][k] = nullptr;
+            return PSA_ECUDA;
+        }
+    *ev = g_ev[dev];
+    return PSA_OK;
+}
+
+}  // namespace
+
+int psa_batch_workspace_bytes(const void *plan_host, const psa_lanczos_opts *opts, int64_t points_in_flight,
+                              int32_t n_streams, size_t *bytes)
+{
+    if (!plan_ok(plan_host) || points_in_flight < 1 || n_streams < 1 || n_streams > kMaxStreams || !bytes)
+        return PSA_EINVAL;
+    const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
+    if (!opts_ok(o)) return PSA_EINVAL;
+    const PlanHeader &H = *static_cast<const PlanHeader *>(plan_host);
+    const PlanClass *C = plan_classes(plan_host);
+    const BatchLayout B = batch_layout(H, n_streams);
+    size_t wmax = 0;
+    for (int c = 0; c < H.nclass; ++c) {
+        const int64_t nw_req = (points_in_flight + 31) / 32;
+        const int64_t nw = nw_req < C[c].ngroups ? nw_req : C[c].ngroups;
+        const size_t w = (size_t)nw * (size_t)layout(C[c].n_max, C[c].kl, C[c].ku, o.k_max, 1, 0).warp_bytes;
+        if (w > wmax) wmax = w;
+    }
+    *bytes = B.regions + (size_t)n_streams * wmax;
+    return PSA_OK;
+}
+
+int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const double *eps, int32_t n_eps,
+                          double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
+                          const psa_lanczos_opts *opts, int64_t points_in_flight, int32_t order, void *workspace,
+                          size_t ws_bytes, void *stream_ptr, void *const *aux_streams, int32_t n_aux)
+{
+    if (!plan_ok(plan_host) || !plan_dev || (reinterpret_cast<uintptr_t>(plan_dev) % kAlign) != 0 || !sigma)
+        return PSA_EINVAL;
+    if (n_eps < 0 || n_eps > kMaxEps || (n_eps > 0 && !eps)) return PSA_EINVAL;
+    for (int l = 0; l < n_eps; ++l)
+        if (!std::isfinite(eps[l]) || !(eps[l] > 0.0)) return PSA_EINVAL;
+    if (points_in_flight < 0 || order < PSA_BATCH_ORDER_AUTO || order > PSA_BATCH_ORDER_ESTIMATE) return PSA_EINVAL;
+    if (n_aux < 0 || n_aux > kMaxStreams - 1 || (n_aux > 0 && !aux_streams)) return PSA_EINVAL;
+    for (int k = 0; k < n_aux; ++k) {
+        if (aux_streams[k] == stream_ptr) return PSA_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (aux_streams[j] == aux_streams[k]) return PSA_EINVAL;
+    }
+    const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
+    if (!opts_ok(o)) return PSA_EINVAL;
+    const PlanHeader &H = *static_cast<const PlanHeader *>(plan_host);
+    const PlanClass *C = plan_classes(plan_host);
+    const PlanMat *Md = reinterpret_cast<const PlanMat *>(static_cast<const char *>(plan_dev) + kPlanMatOff);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PSA_EWORKSPACE;
+    if (H.nmat == 0) return PSA_OK;
+    const int nstreams = 1 + n_aux;
+    const BatchLayout B = batch_layout(H, nstreams);
+    if (ws_bytes <= B.regions) return PSA_EWORKSPACE;
+    const size_t region = (ws_bytes - B.regions) / (size_t)nstreams / kAlign * kAlign;
+
+    // per class: kernel, warps in flight, stream and work-order decision, all checked
+    // before anything is launched
+    struct ClassRun {
+        KernelOps ops;
+        int64_t nwarps;
+        bool ordered;
+        Layout L;
+    } run[kMaxClasses];
+    for (int c = 0; c < H.nclass; ++c) {
+        const PlanClass &pc = C[c];
+        if (pc.kl < 0 || pc.kl > kMaxKL || pc.ku < 0 || pc.ku > kMaxKU || pc.count < 1 || pc.ngroups < 1 ||
+            pc.first < 0 || pc.first + pc.count > H.nmat || pc.ngroups > H.max_ngroups)
+            return PSA_EINVAL;
+        ClassRun &r = run[c];
+        r.ops = pick_ops(pc.kl, pc.ku);
+        if (!r.ops.launch) return PSA_EUNSUPPORTED;
+        const Layout L1 = layout(pc.n_max, pc.kl, pc.ku, o.k_max, 1, 0);
+        int64_t nw = (int64_t)(region / (size_t)L1.warp_bytes);
+        if (nw < 1) return PSA_EWORKSPACE;
+        int64_t full = 0;
+        const int frc = full_threads(r.ops, &full);
+        if (frc != PSA_OK) return frc;
+        if (nw > full / 32) nw = full / 32;
+        if (points_in_flight > 0 && nw > (points_in_flight + 31) / 32) nw = (points_in_flight + 31) / 32;
+        if (nw > pc.ngroups) nw = pc.ngroups;
+        if (nw >= 4) nw = round_down(nw, 4);
+        r.nwarps = nw;
+        r.ordered = order == PSA_BATCH_ORDER_ESTIMATE ? pc.ngroups > 1
+                    : order == PSA_BATCH_ORDER_AUTO   ? pc.ngroups >= 2 * nw && pc.ngroups > 1
+                                                      : false;
+        r.L = L1;
+    }
+    int corder[kMaxClasses], lane[kMaxClasses];
+    stream_schedule(plan_host, H.nclass, nstreams, corder, lane);
+    cudaEvent_t *ev = nullptr;
+    if (nstreams > 1) {
+        const int erc = batch_events(&ev);
+        if (erc != PSA_OK) return erc;
+    }
+
+    cudaStream_t streams[kMaxStreams] = {static_cast<cudaStream_t>(stream_ptr)};
+    for (int k = 0; k < n_aux; ++k) streams[1 + k] = static_cast<cudaStream_t>(aux_streams[k]);
+    char *ws = static_cast<char *>(workspace);
+    int *const counters = reinterpret_cast<int *>(ws + B.counters);
+    int *const mflags = reinterpret_cast<int *>(ws + B.mflags);
+    double2 *const q1 = reinterpret_cast<double2 *>(ws + B.q1);
+
+    if (cudaMemsetAsync(ws, 0, B.q1, streams[0]) != cudaSuccess) return PSA_ECUDA;  // counters and mflags
+    k_batch_start_vectors<<<(unsigned)H.nmat, 256, 0, streams[0]>>>(Md, q1, o.seed);
+    if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+    for (int c = 0; c < H.nclass; ++c) {
+        const PlanClass &pc = C[c];
+        const int64_t total = (int64_t)(pc.kl + pc.ku + 1) * pc.n_max;
+        const int64_t bx = (total + 255) / 256 < 64 ? (total + 255) / 256 : 64;
+        k_batch_check_finite<<<dim3((unsigned)bx, (unsigned)pc.count), 256, 0, streams[0]>>>(Md + pc.first, pc.kl,
+                                                                                            pc.ku, mflags + pc.first);
+        if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+    }
+    if (nstreams > 1) {
+        if (cudaEventRecord(ev[0], streams[0]) != cudaSuccess) return PSA_ECUDA;
+        for (int k = 1; k < nstreams; ++k)
+            if (cudaStreamWaitEvent(streams[k], ev[0], 0) != cudaSuccess) return PSA_ECUDA;
+    }
+
+    for (int r_ = 0; r_ < H.nclass; ++r_) {
+        const int c = corder[r_];
+        const PlanClass &pc = C[c];
+        const ClassRun &r = run[c];
+        const int s = lane[c];
+        cudaStream_t st = streams[s];
+        int *const hist = reinterpret_cast<int *>(ws + B.sched + (size_t)s * B.sched_bytes);
+        int *const cursor = hist + kBuckets;
+        int *const bucket = cursor + kBuckets;
+        int *const order_arr = bucket + H.max_ngroups;
+        KParams p{};
+        p.kl = pc.kl;
+        p.ku = pc.ku;
+        p.pmats = Md + pc.first;
+        p.nmats = pc.count;
+        p.trow = pc.n_max;
+        p.mflags = mflags + pc.first;
+        p.ngroups = pc.ngroups;
+        p.nchunks = pc.nchunks;
+        for (int l = 0; l < kMaxEps; ++l) p.eps[l] = l < n_eps ? eps[l] : 0.0;
+        p.n_eps = n_eps;
+        p.k_min = o.k_min;
+        p.k_max = o.k_max;
+        p.tol = o.tol;
+        p.sigma = sigma;
+        p.mask = mask;  // every point of a batch is evaluated and writes its bits
+        p.status = status;
+        p.steps = steps;
+        p.flags = counters;
+        p.counter = counters + 2 * c;
+        p.estimate = 0;
+        p.order = r.ordered ? order_arr : nullptr;
+        p.sched_bucket = bucket;
+        p.sched_hist = hist;
+        p.q1 = q1;
+        p.wdata = ws + B.regions + (size_t)s * region;
+        p.warp_bytes = r.L.warp_bytes;
+        p.row_bytes = r.L.row_bytes;
+        p.piv_offset = (2 * pc.kl + pc.ku + 1 + 3) * 512;
+        p.P = r.nwarps * 32;
+        if (r.ordered) {
+            if (cudaMemsetAsync(hist, 0, sizeof(int) * kBuckets, st) != cudaSuccess) return PSA_ECUDA;
+            KParams pe = p;
+            pe.estimate = 1;
+            pe.order = nullptr;
+            pe.k_min = pe.k_max = o.k_max < kEstimateSteps ? o.k_max : kEstimateSteps;
+            pe.tol = 0.0;
+            pe.counter = counters + 2 * c + 1;
+            pe.sigma = nullptr;
+            pe.mask = nullptr;
+            pe.status = nullptr;
+            pe.steps = nullptr;
+            if (r.ops.launch(pe, st) != cudaSuccess) return PSA_ECUDA;
+            k_sched_scan<<<1, kScanThreads, 0, st>>>(hist, cursor);
+            if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+            const int64_t sb = (pc.ngroups + 255) / 256 < 4096 ? (pc.ngroups + 255) / 256 : 4096;
+            k_sched_scatter<<<(unsigned)sb, 256, 0, st>>>(bucket, cursor, order_arr, pc.ngroups);
+            if (cudaGetLastError() != cudaSuccess) return PSA_ECUDA;
+        }
+        if (r.ops.launch(p, st) != cudaSuccess) return PSA_ECUDA;
+    }
+    for (int k = 1; k < nstreams; ++k) {
+        if (cudaEventRecord(ev[k], streams[k]) != cudaSuccess) return PSA_ECUDA;
+        if (cudaStreamWaitEvent(streams[0], ev[k], 0) != cudaSuccess) return PSA_ECUDA;
+    }
     return PSA_OK;
 }
 

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
     char *const wbase = p.wdata + warp * p.warp_bytes;
     char *const rows = wbase + lane * 16;
     uint8_t *const pivs = reinterpret_cast<uint8_t *>(wbase) + p.piv_offset + lane;
-    double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)n * RB) + lane;
+    double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)p.trow * RB) + lane;
+    const Mat M = single_mat(p);
     double *const Tb = Ta + (int64_t)p.k_max * 32;
     double *const Tc = Tb + (int64_t)p.k_max * 32;  // eigenvector s, then the coefficients s_j / beta_{j-1}
     double *const Td = Tc + (int64_t)p.k_max * 32;  // LDL^T pivots of x I - T_k
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
             zr = z.x;
             zi = z.y;
         }
-        const bool singular = band_lu<KL, KU>(p, rows, pivs, Aw, lane, zr, zi, bad_input);
+        const bool singular = band_lu<KL, KU>(p, M, rows, pivs, Aw, lane, zr, zi, bad_input);
 
         double sigma = 0.0;
         int status = bad_input ? 3 : 1;
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
         if (have && !singular && !bad_input) {
             LzState st;
             double theta = 0.0;
-            status = lanczos_sigma<KL, KU>(p, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
+            status = lanczos_sigma<KL, KU>(p, M, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
             ok = (status == 0 || status == 2) && sigma > 0.0 && ksteps >= 1;
             if (ok) {
                 // ---- 1. s = top eigenvector of T_k: two steps of inverse iteration on M = x I - T_k
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
                 LzState st2;
                 for (int j = 1; j <= k; ++j) {
                     double a2;
-                    (void)lanczos_step<KL, KU, true>(p, rows, pivs, Ta, Tb, j, st2, a2, Tc[(int64_t)(j - 1) * TS], j == k);
+                    (void)lanczos_step<KL, KU, true>(p, M, rows, pivs, Ta, Tb, j, st2, a2, Tc[(int64_t)(j - 1) * TS], j == k);
                 }
 
                 // ---- 3. u = y / |y| (kept in FY), x = B^{-1} (2^-e1 u) in FX, v = x / |x|

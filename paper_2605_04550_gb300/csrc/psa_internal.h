@@ -10,7 +10,38 @@ constexpr int kMaxEps = 32;
 constexpr int kThreads = 128;        // threads per block of the sigma_min kernel
 constexpr int kMaxKL = 4;            // compile-time band shapes: kl in [0, 4]
 constexpr int kMaxKU = 8;            //                           ku in [0, 8]
-constexpr int kBuckets = 1024;       // log2-sigma buckets of the work order (8 per octave)
+constexpr int kBuckets = 4096;       // cost buckets of the work order (matrix order x sigma)
+constexpr int kMaxStreams = 8;       // batches: the caller's stream and up to 7 auxiliary streams
+
+// One matrix of a batch, as the device plan lists it (psa_batch_plan): matrices of
+// one band shape are consecutive, gstart is the first group of the matrix within
+// its class, q1_off the offset (in complex values) of its start vector in the
+// workspace, out_off the first index of its outputs.
+struct PlanMat {
+    const double2 *bands;
+    int32_t n, nx, ny, pad;
+    double re_min, im_min, hx, hy;
+    int64_t out_off, gstart, q1_off;
+    int64_t estart;  // first estimate chunk (32 anchors of this matrix) within its class
+};
+
+// A band-shape class of a batch plan: matrices first .. first+count-1 of the plan.
+struct PlanClass {
+    int32_t kl, ku, n_max, first, count, pad;
+    int64_t ngroups, nchunks;
+};
+
+// Plan memory (host and device copies are identical): header, kMaxClasses classes,
+// then one PlanMat per matrix (class by class).
+constexpr int kMaxClasses = (kMaxKL + 1) * (kMaxKU + 1);
+constexpr int32_t kPlanMagic = 0x50534142;
+struct PlanHeader {
+    int32_t magic, nmat, nclass, max_n;
+    int64_t q1_total;      // complex values of all start vectors
+    int64_t max_ngroups;   // groups of the largest class
+};
+constexpr size_t kPlanClassOff = 256;
+constexpr size_t kPlanMatOff = kPlanClassOff + ((kMaxClasses * sizeof(PlanClass) + 255) / 256) * 256;
 
 // Everything one launch of the sigma_min kernel needs (passed by value).
 struct KParams {
@@ -20,12 +51,21 @@ struct KParams {
     // grid
     double re_min, im_min, hx, hy;
     int nx, ny;
+    // batch: nmats > 0 -> groups are tiles of the matrices pmats[0 .. nmats) (one band
+    // shape), whose start vectors sit at q1 + pmats[m].q1_off; trow = rows of the
+    // largest matrix (the tridiagonal arrays of a warp block follow them)
+    const PlanMat *pmats;
+    int nmats;
+    int trow;
+    const int *mflags;  // batch: mflags[m] != 0 when matrix m has a non-finite band entry
     // points: idx == nullptr -> flat index = point number; else idx[point]
     const int32_t *idx;
     int64_t npts;
     int64_t ngroups;  // groups of 32 points: 8 x 4 grid tiles (full grid) or list chunks
+    int64_t nchunks;  // estimate pass: chunks of 32 anchors
     // work order: estimate != 0 runs only each group's anchor point for k_max steps
-    // and files the group under a bucket of log2 sigma (sched_bucket, sched_hist);
+    // and files the group under a cost bucket (matrix order, then sigma relative to
+    // the grid's extent: sched_bucket, sched_hist);
     // otherwise warps take groups order[0], order[1], ... (or 0, 1, ... if order is NULL)
     int estimate;
     const int *order;

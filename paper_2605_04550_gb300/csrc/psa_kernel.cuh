@@ -225,6 +225,48 @@ struct Shape {
     static constexpr int MIN_BLOCKS = ((KL + 1) * (KW + 1) <= 24) ? 3 : 2;
 };
 
+// The matrix and grid a group belongs to (the launch's one matrix, or one of a batch).
+struct Mat {
+    const double2 *bands;
+    const double2 *q1;
+    int n, nx, ny;
+    double re_min, im_min, hx, hy;
+    int64_t out_off;
+};
+
+__device__ __forceinline__ Mat single_mat(const KParams &p)
+{
+    return Mat{p.bands, p.q1, p.n, p.nx, p.ny, p.re_min, p.im_min, p.hx, p.hy, 0};
+}
+
+__device__ __forceinline__ Mat plan_mat(const KParams &p, int m)
+{
+    const PlanMat &e = p.pmats[m];
+    return Mat{e.bands, p.q1 + e.q1_off, e.n, e.nx, e.ny, e.re_min, e.im_min, e.hx, e.hy, e.out_off};
+}
+
+// Batch: the matrix whose group range holds global group g (binary search on gstart).
+__device__ __forceinline__ int plan_find(const KParams &p, int64_t g)
+{
+    int lo = 0, hi = p.nmats - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.pmats[mid].gstart <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batch: the matrix whose estimate-chunk range holds chunk c.
+__device__ __forceinline__ int plan_find_chunk(const KParams &p, int64_t c)
+{
+    int lo = 0, hi = p.nmats - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.pmats[mid].estart <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Lanczos scalars carried from step to step (see the kernel's header comment).
 struct LzState {
     double acoef = 0.0;    // v_k = w_{k-1} - acoef v_{k-1}
@@ -240,15 +282,15 @@ struct LzState {
 // Tb and alpha_k in Ta. With ACC, sweep (a) also adds yc * v_k into the field FY (the
 // Ritz vector of the gradient kernel); with only_a the step stops after sweep (a).
 template <int KL, int KU, bool ACC>
-__device__ __forceinline__ int lanczos_step(const KParams &p, char *const rows, uint8_t *const pivs, double *const Ta,
-                                            double *const Tb, const int k, LzState &st, double &alpha, const double yc,
-                                            const bool only_a)
+__device__ __forceinline__ int lanczos_step(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
+                                            double *const Ta, double *const Tb, const int k, LzState &st, double &alpha,
+                                            const double yc, const bool only_a)
 {
     using SH = Shape<KL, KU>;
     constexpr int KW = SH::KW;
     constexpr int FA = SH::FA, FB = SH::FB, FX = SH::FX;
     constexpr int64_t TS = 32;
-    const int n = p.n;
+    const int n = M.n;
     const int RB = p.row_bytes;
 #define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
 #define PIVOF(j) (pivs[(j) * RB])
@@ -270,7 +312,7 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, char *const rows, 
             return v;
         };
         auto load_w = [&](int ii, double2 &w, double2 &vp) {
-            if (first) { w = __ldg(&p.q1[ii]); vp = make_double2(0.0, 0.0); }
+            if (first) { w = __ldg(&M.q1[ii]); vp = make_double2(0.0, 0.0); }
             else { w = FLD(ii, fcur); vp = FLD(ii, fprv); }
         };
 #pragma unroll
@@ -477,12 +519,13 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, char *const rows, 
 // KW superdiagonal entries of U and the KL multipliers. Returns true when a column
 // had no nonzero pivot candidate (B singular).
 template <int KL, int KU>
-__device__ __forceinline__ bool band_lu(const KParams &p, char *const rows, uint8_t *const pivs, double2 (*const Aw)[32],
-                                        const int lane, const double zr, const double zi, const bool bad_input)
+__device__ __forceinline__ bool band_lu(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
+                                        double2 (*const Aw)[32], const int lane, const double zr, const double zi,
+                                        const bool bad_input)
 {
     using SH = Shape<KL, KU>;
     constexpr int KW = SH::KW;
-    const int n = p.n;
+    const int n = M.n;
     const int RB = p.row_bytes;
 #define FLD(j, f) (*reinterpret_cast<double2 *>(rows + (j) * RB + (f) * 512))
 #define PIVOF(j) (pivs[(j) * RB])
@@ -492,7 +535,7 @@ auto stage = [&](int r0) {
 #pragma unroll
     for (int c = 0; c <= KW; ++c) {
         const int r = r0 + lane;
-        Aw[c][lane] = (r < n) ? __ldg(&p.bands[(int64_t)c * n + r]) : make_double2(0.0, 0.0);
+        Aw[c][lane] = (r < n) ? __ldg(&M.bands[(int64_t)c * n + r]) : make_double2(0.0, 0.0);
     }
     __syncwarp();
 };
@@ -574,8 +617,9 @@ for (int j = 0; j < (bad_input ? 0 : n); ++j) {
 // status (0 OK, 2 NOT_CONVERGED, 5 UNDERFLOW) and sets sigma, the steps taken, the
 // final Ritz value theta (in H' units) and the Lanczos scalars st.
 template <int KL, int KU>
-__device__ __forceinline__ int lanczos_sigma(const KParams &p, char *const rows, uint8_t *const pivs, double *const Ta,
-                                             double *const Tb, LzState &st, double &sigma, int &ksteps, double &theta)
+__device__ __forceinline__ int lanczos_sigma(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
+                                             double *const Ta, double *const Tb, LzState &st, double &sigma, int &ksteps,
+                                             double &theta)
 {
     constexpr int64_t TS = 32;
     int status;
@@ -596,7 +640,7 @@ __device__ __forceinline__ int lanczos_sigma(const KParams &p, char *const rows,
     status = 2;  // NOT_CONVERGED
     for (int k = 1;; ++k) {
         double alpha = 0.0;
-        const int rs = lanczos_step<KL, KU, false>(p, rows, pivs, Ta, Tb, k, st, alpha, 0.0, false);
+        const int rs = lanczos_step<KL, KU, false>(p, M, rows, pivs, Ta, Tb, k, st, alpha, 0.0, false);
         if (rs >= 0) { status = rs; break; }
         ksteps = k;
 
@@ -631,35 +675,37 @@ __device__ __forceinline__ int lanczos_sigma(const KParams &p, char *const rows,
 }
 
 // Flat grid index of lane `lane` of group g (-1: no point): on the full grid an
-// 8 x 4 tile (8 abscissae, 4 ordinates), whose neighbouring points take similar
-// Lanczos step counts so the warp's lanes stay busy together; in restricted mode
-// 32 consecutive entries of the list.
-__device__ __forceinline__ int64_t group_point(const KParams &p, int64_t g, int lane, int64_t ngrid)
+// 8 x 4 tile (8 abscissae, 4 ordinates) of M's grid (g counted within M), whose
+// neighbouring points take similar Lanczos step counts so the warp's lanes stay
+// busy together; in restricted mode 32 consecutive entries of the list.
+__device__ __forceinline__ int64_t group_point(const KParams &p, const Mat &M, int64_t g, int lane)
 {
+    const int64_t ngrid = (int64_t)M.nx * M.ny;
     if (p.idx) {
         const int64_t pt = g * 32 + lane;
         if (pt >= p.npts) return -1;
         const int64_t f = (int64_t)p.idx[pt];
         return (f >= 0 && f < ngrid) ? f : -1;
     }
-    const int tiles_x = (p.nx + 7) >> 3;
+    const int tiles_x = (M.nx + 7) >> 3;
     const int ty = (int)(g / tiles_x), tx = (int)(g - (int64_t)ty * tiles_x);
     const int i = ty * 4 + (lane >> 3), j = tx * 8 + (lane & 7);
-    return (i < p.ny && j < p.nx) ? (int64_t)i * p.nx + j : -1;
+    return (i < M.ny && j < M.nx) ? (int64_t)i * M.nx + j : -1;
 }
 
 // A point representative of group g for the work-order estimate: the tile's point
 // (1, 3) (clamped to the grid), or the first entry of a list chunk.
-__device__ __forceinline__ int64_t group_anchor(const KParams &p, int64_t g, int64_t ngrid)
+__device__ __forceinline__ int64_t group_anchor(const KParams &p, const Mat &M, int64_t g)
 {
+    const int64_t ngrid = (int64_t)M.nx * M.ny;
     if (p.idx) {
         const int64_t f = (int64_t)p.idx[g * 32];
         return (f >= 0 && f < ngrid) ? f : -1;
     }
-    const int tiles_x = (p.nx + 7) >> 3;
+    const int tiles_x = (M.nx + 7) >> 3;
     const int ty = (int)(g / tiles_x), tx = (int)(g - (int64_t)ty * tiles_x);
-    const int i = min(ty * 4 + 1, p.ny - 1), j = min(tx * 8 + 3, p.nx - 1);
-    return (int64_t)i * p.nx + j;
+    const int i = min(ty * 4 + 1, M.ny - 1), j = min(tx * 8 + 3, M.nx - 1);
+    return (int64_t)i * M.nx + j;
 }
 
 template <int KL, int KU>
@@ -669,15 +715,12 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
     constexpr int KW = SH::KW;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n = p.n;
     const int RB = p.row_bytes;
-    const int64_t ngrid = (int64_t)p.nx * p.ny;
     char *const wbase = p.wdata + warp * p.warp_bytes;
     char *const rows = wbase + lane * 16;
     uint8_t *const pivs = reinterpret_cast<uint8_t *>(wbase) + p.piv_offset + lane;
-    double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)n * RB) + lane;
+    double *const Ta = reinterpret_cast<double *>(wbase + (int64_t)p.trow * RB) + lane;
     double *const Tb = Ta + (int64_t)p.k_max * 32;
-    const bool bad_input = p.flags[0] != 0;
     __shared__ double2 Aw_all[kThreads / 32][KW + 1][32];
     double2 (*const Aw)[32] = Aw_all[threadIdx.x >> 5];
     double zr = 0.0, zi = 0.0;
@@ -690,18 +733,42 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
         int grp = 0;
         if (lane == 0) grp = atomicAdd(p.counter, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
-        if ((int64_t)grp >= (p.estimate ? (p.ngroups + 31) / 32 : p.ngroups)) break;
+        if ((int64_t)grp >= (p.estimate ? p.nchunks : p.ngroups)) break;
         int64_t flat = -1;
         int64_t anchor_of = -1;  // estimate pass: the group whose anchor this lane runs
+        Mat M;
+        bool bad_input;
         if (p.estimate) {
-            const int64_t a = (int64_t)grp * 32 + lane;
-            if (a < p.ngroups) {
-                anchor_of = a;
-                flat = group_anchor(p, a, ngrid);
+            // the lanes of one warp run the anchors of 32 groups of one matrix
+            int64_t a = (int64_t)grp * 32 + lane, g0 = 0, gn = p.ngroups;
+            if (p.nmats) {
+                const int m = plan_find_chunk(p, grp);
+                M = plan_mat(p, m);
+                bad_input = p.mflags[m] != 0;
+                a = (grp - p.pmats[m].estart) * 32 + lane;
+                g0 = p.pmats[m].gstart;
+                gn = (int64_t)((M.nx + 7) / 8) * ((M.ny + 3) / 4);
+            } else {
+                M = single_mat(p);
+                bad_input = p.flags[0] != 0;
+            }
+            if (a < gn) {
+                anchor_of = g0 + a;
+                flat = group_anchor(p, M, a);
             }
         } else {
             const int64_t g = p.order ? (int64_t)p.order[grp] : (int64_t)grp;
-            flat = group_point(p, g, lane, ngrid);
+            int64_t gl = g;
+            if (p.nmats) {
+                const int m = plan_find(p, g);
+                M = plan_mat(p, m);
+                bad_input = p.mflags[m] != 0;
+                gl = g - p.pmats[m].gstart;
+            } else {
+                M = single_mat(p);
+                bad_input = p.flags[0] != 0;
+            }
+            flat = group_point(p, M, gl, lane);
         }
         // every lane runs the factorisation (lanes without a point on a dummy z), so
         // that the warp can stage the bands of A cooperatively
@@ -711,14 +778,14 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
             atomicAdd(&p.sched_hist[0], 1);
         }
         {
-            const int gi = have ? (int)(flat / p.nx) : 0;
-            const int gj = have ? (int)(flat - (int64_t)gi * p.nx) : 0;
-            zr = fma((double)gj, p.hx, p.re_min);
-            zi = fma((double)gi, p.hy, p.im_min);
+            const int gi = have ? (int)(flat / M.nx) : 0;
+            const int gj = have ? (int)(flat - (int64_t)gi * M.nx) : 0;
+            zr = fma((double)gj, M.hx, M.re_min);
+            zi = fma((double)gi, M.hy, M.im_min);
         }
 
         // ---------------- 1. banded LU with partial pivoting
-        const bool singular = band_lu<KL, KU>(p, rows, pivs, Aw, lane, zr, zi, bad_input);
+        const bool singular = band_lu<KL, KU>(p, M, rows, pivs, Aw, lane, zr, zi, bad_input);
 
         if (have) {
             double sigma = 0.0;
@@ -727,22 +794,29 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
             if (!singular && !bad_input) {
                 LzState st;
                 double theta = 0.0;
-                status = lanczos_sigma<KL, KU>(p, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
+                status = lanczos_sigma<KL, KU>(p, M, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
             }
 
             // ---------------- 4. outputs
             if (p.estimate) {
-                // file the group under log2(sigma estimate), 8 buckets per octave; points
-                // far from the spectrum take the most Lanczos steps, so groups are later
-                // taken in decreasing bucket order (longest first)
+                // file the group under its estimated cost: the matrix order n (two buckets
+                // per octave) and then sigma relative to the grid's extent (8 buckets per
+                // octave over [2^-8, 1]): points far from the spectrum take the most
+                // Lanczos steps. Groups are later taken in decreasing bucket order.
                 int b = 0;
-                if ((status == 0 || status == 2) && sigma > 0.0)
-                    b = clampi(8 * (exp_field(sigma) - 1023) + ((__double2hiint(sigma) >> 17) & 7) + kBuckets / 2, 1,
-                               kBuckets - 1);
+                if ((status == 0 || status == 2) && sigma > 0.0) {
+                    const double ext = fmax(M.hx * (double)(M.nx - 1), M.hy * (double)(M.ny - 1));
+                    const double rel = ext > 0.0 ? sigma / ext : sigma;
+                    const int sb = clampi(8 * (exp_field(rel) - 1023) + ((__double2hiint(rel) >> 17) & 7) + 64, 1, 63);
+                    const int nb = clampi(2 * (exp_field((double)M.n) - 1023) + ((__double2hiint((double)M.n) >> 19) & 1), 0,
+                                          kBuckets / 64 - 1);
+                    b = nb * 64 + sb;
+                }
                 p.sched_bucket[anchor_of] = b;
                 atomicAdd(&p.sched_hist[b], 1);
                 continue;
             }
+            flat += M.out_off;
             p.sigma[flat] = sigma;
             if (p.mask) {
                 uint32_t bits = 0;

@@ -21,6 +21,9 @@ Workloads (all synthetic, seeded):
   (Sec. 3.3, Eq. (matrix)): n = 64, beta uniform in {1,2,3,4}, entries uniform
   in {-1, 0, 1} for |i - j| <= beta, redrawn while A == A^T or
   cond(A) >= 1e8 (best-conditioned draw when no draw qualifies).
+* ``batch_workload(nmat, seed)`` -- a batch of Grcar-type and random-Toeplitz
+  matrices of log-uniform order and random band shape, with 1e-3 band noise,
+  each on its own grid.
 * normal matrices with known spectra, used by the closed-form checks.
 """
 from __future__ import annotations
@@ -43,6 +46,8 @@ __all__ = [
     "jordan_block",
     "grcar_grid_100",
     "paper_grid_100",
+    "grcar_type",
+    "batch_workload",
 ]
 
 
@@ -113,12 +118,14 @@ def random_toeplitz(n: int, kl: int, ku: int, seed: int, super_scale: float = 4.
 
 
 def toeplitz_symbol_grid(a: np.ndarray, kl: int, ku: int, nx: int, ny: int,
-                         pad: float = 0.2, samples: int = 4096) -> Grid:
+                         pad: float = 0.2, samples: int = 4096, min_aspect: float = 0.0) -> Grid:
     """Grid over the bounding box of the symbol curve, widened by ``pad``.
 
     The symbol is f(t) = sum_d a_d exp(i d t) sampled at ``samples`` points of
     [0, 2 pi); the box keeps its centre and its width and height grow by the
-    factor 1 + pad.
+    factor 1 + pad. With ``min_aspect`` > 0 the shorter side is widened to at
+    least min_aspect times the longer one (a symbol curve that is a segment,
+    as for kl = ku Grcar-type bands, still gets a two-dimensional box).
     """
     t = np.arange(samples) * (2.0 * np.pi / samples)
     d = np.arange(-kl, ku + 1)
@@ -127,6 +134,7 @@ def toeplitz_symbol_grid(a: np.ndarray, kl: int, ku: int, nx: int, ny: int,
     cy = 0.5 * (f.imag.min() + f.imag.max())
     hw = 0.5 * (f.real.max() - f.real.min()) * (1.0 + pad)
     hh = 0.5 * (f.imag.max() - f.imag.min()) * (1.0 + pad)
+    hw, hh = max(hw, min_aspect * hh), max(hh, min_aspect * hw)
     return Grid(float(cx - hw), float(cx + hw), float(cy - hh), float(cy + hh), nx, ny)
 
 
@@ -220,6 +228,47 @@ def grcar_perturbed(n: int, seed: int, scale: float = 1e-2):
     rng = np.random.Generator(np.random.PCG64(seed))
     b = b + scale * rng.standard_normal(b.shape)
     return _zero_outside(b.astype(np.complex128), n, kl, ku), kl, ku
+
+
+def grcar_type(n: int, kl: int, ku: int) -> np.ndarray:
+    """Grcar-type band: -1 on the kl subdiagonals, +1 on the diagonal and the ku
+    superdiagonals (the Grcar matrix is kl = 1, ku = 3)."""
+    b = _empty_bands(n, kl, ku)
+    b[:kl, :] = -1.0
+    b[kl:, :] = 1.0
+    return _zero_outside(b, n, kl, ku)
+
+
+def batch_workload(nmat: int = 256, seed: int = 0, n_min: int = 200, n_max: int = 8000,
+                   nx: int = 128, ny: int = 128, noise: float = 1e-3):
+    """Seeded batch of banded matrices of uneven order and band shape, each with its grid.
+
+    Per matrix m (one PCG64 stream per batch): n = round(exp(U(log n_min, log n_max)))
+    (log-uniform), kl uniform in {1..4}, ku uniform in {1..8}, the type Grcar-type or
+    random Toeplitz (``toeplitz_coefficients`` with seed ``seed * 100003 + m``) with
+    probability 1/2 each, then every band entry plus complex Gaussian noise
+    noise * (N(0,1) + i N(0,1)). The grid is nx x ny over the bounding box of the
+    coefficient symbol widened by 20 %, its shorter side at least half the
+    longer (``toeplitz_symbol_grid`` with min_aspect = 0.5).
+    Returns a list of (bands, kl, ku, grid, kind).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in range(nmat):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        kl = int(rng.integers(1, 5))
+        ku = int(rng.integers(1, 9))
+        if rng.random() < 0.5:
+            kind = "grcar"
+            a = np.concatenate([-np.ones(kl), np.ones(ku + 1)]).astype(np.complex128)
+            b = grcar_type(n, kl, ku)
+        else:
+            kind = "toeplitz"
+            b, _, _, a = random_toeplitz(n, kl, ku, seed=seed * 100003 + m)
+        b = b + noise * (rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape))
+        b = _zero_outside(b.astype(np.complex128), n, kl, ku)
+        out.append((b, kl, ku, toeplitz_symbol_grid(a, kl, ku, nx, ny, min_aspect=0.5), kind))
+    return out
 
 
 def grcar_grid_100() -> Grid:

@@ -65,10 +65,11 @@ def test_workspace_bytes_layout(lib):
     assert expect <= b <= expect + (P // 32) * (n * (128 - 32) + 256) + 256
     # rounded up to whole warps
     assert _ws(lib, 2000, 2, 5, 97)[1] == _ws(lib, 2000, 2, 5, 128)[1]
-    # the work-order schedule: 8 KB + 8 bytes per group, at most npoints / 8 + 2 groups
+    # the work-order schedule: 32 KB (histogram and cursors of 4096 buckets) + 8 bytes
+    # per group, at most npoints / 8 + 2 groups
     npts = 262144
     extra = _ws(lib, 2000, 2, 5, 128, npoints=npts)[1] - b
-    assert 8192 + 8 * (npts // 8 + 2) <= extra <= 8192 + 8 * (npts // 8 + 2) + 256
+    assert 32768 + 8 * (npts // 8 + 2) <= extra <= 32768 + 8 * (npts // 8 + 2) + 256
 
 
 @pytest.mark.parametrize("n,kl,ku,P,npts", [(0, 0, 0, 32, 0), (5, 5, 0, 32, 0), (5, 0, 5, 32, 0), (5, -1, 0, 32, 0),
