@@ -333,6 +333,54 @@ int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const dou
                           void *workspace, size_t ws_bytes, void *stream, void *const *aux_streams,
                           int32_t n_aux);
 
+/* --------------------------------------------------------------- classifier
+ * The learned restriction of the hybrid method (paper Sec. 3-4): a network maps
+ * per-point features to the probability that the point is sensitive; only the
+ * points it selects get the exact sigma_min evaluation. Here the network is a
+ * multilayer perceptron IN -> 256 -> 256 -> 256 -> 1 (SiLU hidden units,
+ * sigmoid output) whose dense layers run as BF16 GEMMs on the tensor cores
+ * with FP32 accumulation; training minimises binary cross-entropy with Adam
+ * (Sec. 3.4). Parameters are one float32 vector theta (device) laid out as
+ * W1[256][IN], b1[256], W2[256][256], b2[256], W3[256][256], b3[256],
+ * w4[256], b4 (W[out][in], row-major). Features are BF16 rows of IN values
+ * (the feature kernels of psa_features.cu fill them). */
+#define PSA_MLP_IN 128
+#define PSA_MLP_HIDDEN 256
+#define PSA_MLP_PARAMS 164865
+
+/* C[M][N] (float32, row-major, leading dimension ldc) = A[M][K] * B[N][K]^T
+ * with A and B BF16 (raw uint16 bits) row-major, K contiguous, on the tensor
+ * cores (FP32 accumulation). Device pointers, 16-byte aligned; N a multiple
+ * of 128, K a multiple of 64, lda and ldb multiples of 8; M any.
+ * Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
+                  float *C, int64_t ldc, void *stream);
+
+/* Bytes of device workspace for psa_mlp_forward over `rows` rows (training = 0;
+ * rows beyond 131072 are processed in passes of 131072) or for
+ * psa_mlp_train_step on batches of `rows` rows (training = 1). Host call.
+ * Errors: PSA_EINVAL. */
+int psa_mlp_workspace_bytes(int64_t rows, int32_t training, size_t *bytes);
+
+/* prob[r] = network(x[r]) for r < rows: x DEVICE BF16 [rows][IN] (16-byte
+ * aligned), prob DEVICE float32 [rows], theta DEVICE float32
+ * [PSA_MLP_PARAMS]; workspace DEVICE, 256-byte aligned, of ws_bytes >=
+ * psa_mlp_workspace_bytes(rows, 0). Asynchronous on stream.
+ * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_ECUDA. */
+int psa_mlp_forward(const float *theta, const uint16_t *x, int64_t rows, float *prob, void *workspace,
+                    size_t ws_bytes, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, epsilon 1e-8, bias-corrected with the
+ * 1-based step number `step`, learning rate lr) on the mean binary
+ * cross-entropy of a batch: x DEVICE BF16 [rows][IN], y DEVICE float32 labels
+ * in [0, 1]; theta, adam_m, adam_v DEVICE float32 [PSA_MLP_PARAMS] updated in
+ * place; *loss (DEVICE float32) receives the batch's mean loss before the
+ * step. rows a multiple of 128. Asynchronous on stream; no allocation, so a
+ * step can be captured in a CUDA graph (step and lr are then fixed at capture).
+ * Errors: PSA_EINVAL, PSA_EWORKSPACE, PSA_ECUDA. */
+int psa_mlp_train_step(float *theta, float *adam_m, float *adam_v, int32_t step, float lr, const uint16_t *x,
+                       const float *y, int64_t rows, float *loss, void *workspace, size_t ws_bytes, void *stream);
+
 /* Measured FP64 throughput of this device: runs a kernel of independent DFMA
  * chains (iters iterations, 8 chains, SM count x 16 warps) on `stream`,
  * synchronises it and returns the rate in DFMA lane-operations per second in

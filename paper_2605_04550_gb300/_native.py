@@ -32,8 +32,14 @@ EXPORTS = (
     "psa_batch_plan",
     "psa_batch_workspace_bytes",
     "psa_sigma_min_batched",
+    "psa_gemm_bf16",
+    "psa_mlp_workspace_bytes",
+    "psa_mlp_forward",
+    "psa_mlp_train_step",
     "psa_probe_dfma_rate",
 )
+
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 128, 256, 164865
 
 BATCH_ORDER_AUTO, BATCH_ORDER_PLAN, BATCH_ORDER_ESTIMATE = 0, 1, 2
 
@@ -116,6 +122,15 @@ def load(path: str | None = None):
         lib.psa_sigma_min_batched.argtypes = [vp, vp, ctypes.POINTER(dbl), i32, vp, vp, vp, vp,
                                               ctypes.POINTER(PsaLanczosOpts), i64, i32, vp, ctypes.c_size_t, vp,
                                               ctypes.POINTER(vp), i32]
+        f32 = ctypes.c_float
+        lib.psa_gemm_bf16.restype = ctypes.c_int
+        lib.psa_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, vp, i64, vp]
+        lib.psa_mlp_workspace_bytes.restype = ctypes.c_int
+        lib.psa_mlp_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_mlp_forward.restype = ctypes.c_int
+        lib.psa_mlp_forward.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        lib.psa_mlp_train_step.restype = ctypes.c_int
+        lib.psa_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         _lib = lib
