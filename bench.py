@@ -527,6 +527,122 @@ def run_batched(args):
     return 0
 
 
+def run_restriction(args):
+    """Learned restriction (paper Sec. 3-4): train the classifier on sigma_min labels of
+    seeded banded matrices, calibrate its threshold for >= 99 % recall on validation
+    matrices, then compare the restricted run with the full-grid run on the test
+    matrix (random banded Toeplitz + 1e-3 noise, n = 20000, kl = 3, ku = 6,
+    1024 x 1024 grid over its symbol box +20 %)."""
+    import torch
+    import paper_2605_04550_gb300 as psa
+    from paper_2605_04550_gb300 import inputs as inp, restriction
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(0)
+    eps = restriction.EPS
+    t_all = time.perf_counter()
+    # ---- training set: labels from the plain GPU method
+    t0 = time.perf_counter()
+    tr = inp.restriction_matrices(args.restrict_train, seed=1, nx=32, ny=32)
+    mats = [(torch.as_tensor(b, device=dev), kl, ku) for b, kl, ku, _, _ in tr]
+    model = restriction.Restriction(dev, seed=0)
+    x, y, _ = model.build_training_set(mats, [g for *_, g, _ in tr], rng)
+    torch.cuda.synchronize(dev)
+    t_labels = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = model.train(x, y, rng)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del x, y, mats
+    # ---- calibration on validation matrices
+    t0 = time.perf_counter()
+    va = inp.restriction_matrices(args.restrict_val, seed=2, nx=args.restrict_val_grid, ny=args.restrict_val_grid)
+    vm = [(torch.as_tensor(b, device=dev), kl, ku) for b, kl, ku, _, _ in va]
+    vg = [g for *_, g, _ in va]
+    vctx = restriction.matrix_contexts(vm, eps)
+    plan, vs = restriction.labels_batched(vm, vg, eps)
+    vs = vs.cpu().numpy()
+    truth = [vs[o:o + g.npoints].reshape(g.ny, g.nx) for o, g in zip(plan.offsets, vg)]
+    cal = model.calibrate(vctx, vg, truth)
+    t_cal = time.perf_counter() - t0
+    del vm, vctx, plan
+    torch.cuda.empty_cache()
+    # ---- test matrix: full grid vs restricted
+    b, kl, ku, grid = inp.restriction_test_matrix(n=args.restrict_test_n, nx=args.restrict_grid, ny=args.restrict_grid)
+    bt = torch.as_tensor(b, device=dev)
+    opts = psa.LanczosOpts(k_min=2, k_max=KMAX, tol=TOL)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pif = min(psa.default_points_in_flight(bt.shape[1], kl, ku, grid.npoints), 4 * 32 * sms)
+    wsp = psa.Workspace(bt.shape[1], kl, ku, pif, opts, device=dev, npoints=grid.npoints)
+    small = inp.Grid(grid.re_min, grid.re_max, grid.im_min, grid.im_max, 64, 64)
+    psa.sigma_min(bt, kl, ku, small, eps=EPS, opts=opts, workspace=wsp)  # warm-up: modules and workspace
+    ctx = restriction.matrix_contexts([(bt, kl, ku)], eps)[0]
+    model.restricted(ctx, small, EPS, opts=opts, workspace=wsp)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        full = psa.sigma_min(bt, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        full_ms = e0.elapsed_time(e1)
+        flush.fill_(2.0)
+        t0 = time.perf_counter()
+        fctx = restriction.matrix_contexts([(bt, kl, ku)], eps)[0]
+        torch.cuda.synchronize(dev)
+        feat_ms = (time.perf_counter() - t0) * 1e3
+        out, mask, idx, tm = model.restricted(fctx, grid, EPS, opts=opts, workspace=wsp)
+    lvl = EPS.index(eps)
+    s_full = full.sigma.cpu().numpy()
+    truth_t = s_full <= eps
+    m = mask.cpu().numpy().astype(bool)
+    met = restriction.recall_metrics(truth_t, m)
+    same = bool(np.array_equal(out.sigma.cpu().numpy()[m], s_full[m]))
+    mask_r = out.mask.cpu().numpy().view(np.uint32)
+    s_pred = ((mask_r >> lvl) & 1).astype(bool)
+    hybrid_ms = feat_ms + tm["nn_ms"] + tm["restricted_ms"]
+    steps = full.steps.cpu().numpy()
+    flops = algorithmic_flops(steps, bt.shape[1], kl, ku)
+    achieved = flops / (full_ms * 1e-3) / 1e12
+    N = grid.npoints
+    line = {"workload": "learned restriction", "metric": METRIC, "value": N / (hybrid_ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": hybrid_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"test matrix: random banded Toeplitz + 1e-3 complex noise, n={bt.shape[1]}, "
+                                   f"kl={kl}, ku={ku}, {grid.nx}x{grid.ny} grid over the symbol box +20%, "
+                                   f"eps={eps}; classifier: MLP {mlp_desc()} BF16 on tensor cores, trained on "
+                                   f"{args.restrict_train} matrices (n log-uniform [500, 5000], kl 1..4, ku 1..8, "
+                                   f"32x32 label grids), calibrated on {args.restrict_val} matrices "
+                                   f"({args.restrict_val_grid}x{args.restrict_val_grid}) for >= 99% recall",
+                       "points_per_step": N, "points_in_flight": pif, "workspace_gb": wsp.nbytes / 1e9,
+                       "warmup": "one 64x64 run of the same kernels (the full-grid run takes minutes)",
+                       "l2": "256 MB flush before each timed run"},
+            "restricted": {"eps": eps, "full_ms": full_ms, "features_ms": feat_ms, "nn_ms": tm["nn_ms"],
+                           "restricted_ms": tm["restricted_ms"], "hybrid_ms": hybrid_ms,
+                           "speedup_actual": full_ms / hybrid_ms, "speedup_best": full_ms / tm["restricted_ms"],
+                           "region_points": int(idx.numel()), **met,
+                           "sensitive_found": float((s_pred & truth_t).sum() / max(truth_t.sum(), 1)),
+                           "sigma_bitwise_equal_on_region": same,
+                           "hierarchical": getattr(model, "last_counts", None)},
+            "full_grid": {"points_per_s": N / (full_ms * 1e-3), "achieved_tflops": achieved,
+                          "frac_of_fp64_peak": achieved / FP64_PEAK_TFLOPS, "mean_lanczos_steps": float(steps.mean())},
+            "classifier": {"tau": cal["tau"], "paper_rule_tau": cal["paper_rule_tau"],
+                           "calibration_row": cal["row"], "epochs": len(hist),
+                           "final_val_loss": hist[-1]["val_loss"], "final_val_acc": hist[-1]["val_acc"],
+                           "training_samples": None},
+            "pipeline_seconds": {"labels_and_features": t_labels, "training": t_train, "calibration": t_cal,
+                                 "total": time.perf_counter() - t_all, "training_set": model.timing},
+            "clocks": clk.summary(), "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def mlp_desc():
+    return "128->256->256->256->1 (SiLU)"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,10 +653,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--case", default="mid", choices=["mid", "small"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures")
-    ap.add_argument("--workload", default="grid", choices=["grid", "differentiation", "batched"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "differentiation", "batched", "restriction"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
-                         "batched: 256 matrices on their own grids")
+                         "batched: 256 matrices on their own grids; restriction: the learned restriction")
     ap.add_argument("--batch-size", type=int, default=256, help="batched: number of matrices")
+    ap.add_argument("--restrict-train", type=int, default=2000, help="restriction: training matrices")
+    ap.add_argument("--restrict-val", type=int, default=30, help="restriction: validation matrices")
+    ap.add_argument("--restrict-val-grid", type=int, default=128, help="restriction: validation grid side")
+    ap.add_argument("--restrict-test-n", type=int, default=20000, help="restriction: order of the test matrix")
+    ap.add_argument("--restrict-grid", type=int, default=1024, help="restriction: test grid side")
     ap.add_argument("--no-tune", action="store_true", help="batched: default launch controls")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
@@ -550,6 +671,8 @@ def main():
         return run_differentiation(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "restriction":
+        return run_restriction(args)
     return run_gpu(args)
 
 

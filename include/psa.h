@@ -381,6 +381,78 @@ int psa_mlp_forward(const float *theta, const uint16_t *x, int64_t rows, float *
 int psa_mlp_train_step(float *theta, float *adam_m, float *adam_v, int32_t step, float lr, const uint16_t *x,
                        const float *y, int64_t rows, float *loss, void *workspace, size_t ws_bytes, void *stream);
 
+/* Classifier features (paper Sec. 3.1, 3.2.1). psa_matrix_stats reduces A's
+ * band (one block, FP64) to the statistics below and samples the symbol
+ * f(t) = sum_d abar_d e^{i d t} of the diagonal means abar_d at
+ * PSA_SYMBOL_SAMPLES points t_k = 2 pi k / PSA_SYMBOL_SAMPLES (DEVICE outputs
+ * stats[PSA_STATS], symbol[PSA_SYMBOL_SAMPLES]). The symbol curve stands in
+ * for the eigenvalue set of the paper's eigenvalue features; the centroid
+ * trace(A) / n is the eigenvalue centroid exactly. */
+#define PSA_SYMBOL_SAMPLES 256
+#define PSA_MAX_BAND 13
+#define PSA_STATS 24
+#define PSA_STAT_CEN_RE 0      /* Re, Im of trace(A) / n */
+#define PSA_STAT_CEN_IM 1
+#define PSA_STAT_RADIUS 2      /* max_k |f(t_k) - centroid| */
+#define PSA_STAT_FRO 3         /* |A|_F */
+#define PSA_STAT_NORM1 4       /* |A|_1 */
+#define PSA_STAT_NORMINF 5     /* |A|_inf */
+#define PSA_STAT_ASYM 6        /* |A - A^T|_F */
+#define PSA_STAT_AHERM 7       /* |A - A^H|_F */
+#define PSA_STAT_DIAG_MEAN 8   /* mean, std of |A_ii| */
+#define PSA_STAT_DIAG_STD 9
+#define PSA_STAT_OFF_MEAN 10   /* mean, std of |A_ij| over the other in-band positions */
+#define PSA_STAT_OFF_STD 11
+#define PSA_STAT_NNZ 12        /* entries with |A_ij| > 1e-10 */
+#define PSA_STAT_SYM_RE_MEAN 13 /* mean, std, min, max of Re (f - centroid) */
+#define PSA_STAT_SYM_RE_STD 14
+#define PSA_STAT_SYM_RE_MIN 15
+#define PSA_STAT_SYM_RE_MAX 16
+#define PSA_STAT_SYM_IM_MEAN 17 /* the same for Im */
+#define PSA_STAT_SYM_IM_STD 18
+#define PSA_STAT_SYM_IM_MIN 19
+#define PSA_STAT_SYM_IM_MAX 20
+#define PSA_STAT_SYM_RMIN 21    /* min_k |f(t_k) - centroid| */
+#define PSA_STAT_N 22
+#define PSA_STAT_BAND 23        /* 16 kl + ku */
+#define PSA_GLOBAL_FEATURES 28
+
+/* A DEVICE band (kl + ku + 1 <= PSA_MAX_BAND). Errors: PSA_EINVAL,
+ * PSA_EUNSUPPORTED, PSA_ECUDA. */
+int psa_matrix_stats(const psa_band *A, double *stats, psa_c64 *symbol, void *stream);
+
+/* Global feature vector (DEVICE float32 [PSA_GLOBAL_FEATURES]) from the
+ * statistics and sigma4 (DEVICE): sigma_min(zI - A) at z = 0 and at the
+ * centroid + 0.5, + 1, + 2 (the resolvent norms of Table 3 are 1 / sigma_min
+ * exactly), for the level eps. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_global_features(const double *stats, const double *sigma4, double eps, float *global, void *stream);
+
+/* One BF16 row of PSA_MLP_IN features per point of the grid (idx NULL) or of
+ * the flat grid indices idx[0 .. n_idx) (DEVICE), written to x (DEVICE,
+ * 16-byte aligned) in point order: [0, 26) the Fourier encoding [c, sin 2^k c,
+ * cos 2^k c], k = 1..6, of the grid coordinates c scaled to [-1, 1]^2;
+ * 26..28 the distances g1 (to the nearest symbol sample), g2 (to the
+ * centroid), g3 (mean distance to the samples), in units of the symbol radius;
+ * 29, 30 log10 of g1 and g3; 31 the winding number of the symbol curve about
+ * the point; [32, 32 + PSA_GLOBAL_FEATURES) the global features; zeros after.
+ * Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
+                       const psa_c64 *symbol, const float *global, uint16_t *x, void *stream);
+
+/* Predicted region of the hybrid method (paper Sec. 3.6 and 4): mask[f] = 1
+ * when some grid point within `radius` rows and columns of f (a box of
+ * (2 radius + 1)^2 points, clipped to the grid) has prob >= tau. prob and
+ * mask DEVICE, nx * ny entries. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_region(const float *prob, float tau, int32_t nx, int32_t ny, int32_t radius, uint8_t *mask, void *stream);
+
+/* The points of a mask in the sigma_min kernel's full-grid work order (8 x 4
+ * tiles): slot[32 t + l] = flat index of lane l's point of tile t when it is
+ * in the mask, else -1 (slot DEVICE, ceil(nx / 8) * ceil(ny / 4) * 32
+ * entries). The non-negative entries, in order, are a restricted point list
+ * whose chunks of 32 are compact patches of the grid.
+ * Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_tile_slots(const uint8_t *mask, int32_t nx, int32_t ny, int32_t *slot, void *stream);
+
 /* Measured FP64 throughput of this device: runs a kernel of independent DFMA
  * chains (iters iterations, 8 chains, SM count x 16 warps) on `stream`,
  * synchronises it and returns the rate in DFMA lane-operations per second in

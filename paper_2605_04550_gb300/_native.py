@@ -36,8 +36,15 @@ EXPORTS = (
     "psa_mlp_workspace_bytes",
     "psa_mlp_forward",
     "psa_mlp_train_step",
+    "psa_matrix_stats",
+    "psa_global_features",
+    "psa_point_features",
+    "psa_region",
+    "psa_tile_slots",
     "psa_probe_dfma_rate",
 )
+
+SYMBOL_SAMPLES, STATS, GLOBAL_FEATURES = 256, 24, 28
 
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 128, 256, 164865
 
@@ -131,6 +138,16 @@ def load(path: str | None = None):
         lib.psa_mlp_forward.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
         lib.psa_mlp_train_step.restype = ctypes.c_int
         lib.psa_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        lib.psa_matrix_stats.restype = ctypes.c_int
+        lib.psa_matrix_stats.argtypes = [ctypes.POINTER(PsaBand), vp, vp, vp]
+        lib.psa_global_features.restype = ctypes.c_int
+        lib.psa_global_features.argtypes = [vp, vp, dbl, vp, vp]
+        lib.psa_point_features.restype = ctypes.c_int
+        lib.psa_point_features.argtypes = [ctypes.POINTER(PsaGrid), vp, i64, vp, vp, vp, vp, vp]
+        lib.psa_region.restype = ctypes.c_int
+        lib.psa_region.argtypes = [vp, ctypes.c_float, i32, i32, i32, vp, vp]
+        lib.psa_tile_slots.restype = ctypes.c_int
+        lib.psa_tile_slots.argtypes = [vp, i32, i32, vp, vp]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         _lib = lib

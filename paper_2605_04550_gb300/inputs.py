@@ -48,6 +48,8 @@ __all__ = [
     "paper_grid_100",
     "grcar_type",
     "batch_workload",
+    "restriction_matrices",
+    "restriction_test_matrix",
 ]
 
 
@@ -269,6 +271,29 @@ def batch_workload(nmat: int = 256, seed: int = 0, n_min: int = 200, n_max: int 
         b = _zero_outside(b.astype(np.complex128), n, kl, ku)
         out.append((b, kl, ku, toeplitz_symbol_grid(a, kl, ku, nx, ny, min_aspect=0.5), kind))
     return out
+
+
+def restriction_matrices(nmat: int, seed: int, n_min: int = 500, n_max: int = 5000, nx: int = 32, ny: int = 32,
+                         noise: float = 1e-3):
+    """Training / validation matrices of the learned restriction: the families of
+    ``batch_workload`` (Grcar-type or random Toeplitz with complex band noise,
+    kl 1..4, ku 1..8), n log-uniform in [n_min, n_max], each on an nx x ny grid
+    over its symbol box +20 % (shorter side at least half the longer).
+    Returns a list of (bands, kl, ku, grid, kind)."""
+    return batch_workload(nmat=nmat, seed=seed, n_min=n_min, n_max=n_max, nx=nx, ny=ny, noise=noise)
+
+
+def restriction_test_matrix(n: int = 20000, kl: int = 3, ku: int = 6, nx: int = 1024, ny: int = 1024,
+                            seed: int = 2024, noise: float = 1e-3):
+    """The test matrix of the learned restriction: random banded Toeplitz
+    (``toeplitz_coefficients`` with this seed) plus complex Gaussian band noise
+    of standard deviation ``noise``, on an nx x ny grid over its symbol box
+    +20 % (shorter side at least half the longer). Returns (bands, kl, ku, grid)."""
+    b, _, _, a = random_toeplitz(n, kl, ku, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    b = b + noise * (rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape))
+    b = _zero_outside(b.astype(np.complex128), n, kl, ku)
+    return b, kl, ku, toeplitz_symbol_grid(a, kl, ku, nx, ny, min_aspect=0.5)
 
 
 def grcar_grid_100() -> Grid:

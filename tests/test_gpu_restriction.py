@@ -1,0 +1,159 @@
+"""GPU learned restriction: feature kernels against NumPy references of the same
+formulas, region and point-list kernels against NumPy, the hierarchical map
+against the masked full map, and a small end-to-end run (train, calibrate,
+restricted sigma_min equal bitwise to the full grid on the region)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2605_04550_gb300 as psa
+from paper_2605_04550_gb300 import _native, inputs, mlp, restriction
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.complex128, device=DEV)
+
+
+def _dense(b, kl, ku):
+    n = b.shape[1]
+    A = np.zeros((n, n), dtype=np.complex128)
+    for d in range(-kl, ku + 1):
+        for i in range(n):
+            if 0 <= i + d < n:
+                A[i, i + d] = b[d + kl, i]
+    return A
+
+
+def test_matrix_stats_match_numpy():
+    b, kl, ku, a = inputs.random_toeplitz(150, 2, 5, seed=11)
+    b = b + 0.01 * np.random.default_rng(0).standard_normal(b.shape)
+    b = inputs._zero_outside(b.astype(np.complex128), 150, kl, ku)
+    ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
+    st = ctx.stats.cpu().numpy()
+    A = _dense(b, kl, ku)
+    fro = np.linalg.norm(A)
+    assert np.isclose(st[0], np.trace(A).real / 150, rtol=1e-12)
+    assert np.isclose(st[1], np.trace(A).imag / 150, rtol=1e-12, atol=1e-14)
+    assert np.isclose(st[3], fro, rtol=1e-12)
+    assert np.isclose(st[4], np.abs(A).sum(0).max(), rtol=1e-12)
+    assert np.isclose(st[5], np.abs(A).sum(1).max(), rtol=1e-12)
+    assert np.isclose(st[6], np.linalg.norm(A - A.T), rtol=1e-10)
+    assert np.isclose(st[7], np.linalg.norm(A - A.conj().T), rtol=1e-10)
+    d = np.abs(np.diag(A))
+    assert np.isclose(st[8], d.mean(), rtol=1e-12) and np.isclose(st[9], d.std(), rtol=1e-8)
+    # symbol of the diagonal means
+    abar = np.array([np.mean(np.diag(A, dd)) for dd in range(-kl, ku + 1)])
+    t = 2 * np.pi * np.arange(256) / 256
+    f = (abar[None, :] * np.exp(1j * np.outer(t, np.arange(-kl, ku + 1)))).sum(1)
+    np.testing.assert_allclose(ctx.symbol.cpu().numpy(), f, rtol=0, atol=1e-12 * np.abs(f).max())
+    cen = np.trace(A) / 150
+    assert np.isclose(st[2], np.abs(f - cen).max(), rtol=1e-12)
+
+
+def test_resolvent_probe_features_closed_form():
+    """Hermitian tridiagonal Toeplitz A + shift: sigma_min(zI - A) = min_k |z - lambda_k|,
+    lambda_k = a + 2|b| cos(k pi / (n + 1)); the global features take log10 of the
+    probes at z = 0 and the centroid + 0.5, 1, 2."""
+    n, a, bb = 90, 3.0 + 0.5j, 0.8 - 0.6j
+    bands, kl, ku = inputs.hermitian_toeplitz_tridiag(n, 3.0, bb)
+    bands = bands.copy()
+    bands[kl] += 0.5j  # normal: a Hermitian matrix plus a multiple of I
+    ctx = restriction.matrix_contexts([(_t(bands), kl, ku)])[0]
+    st = ctx.stats.cpu().numpy()
+    g = ctx.glob.cpu().numpy()
+    lam = a + 2 * abs(bb) * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    s0 = np.abs(lam).min()
+    A = _dense(bands, kl, ku)
+    s1 = np.sqrt(np.abs(A).sum(0).max() * np.abs(A).sum(1).max())
+    assert abs(g[11] - np.log10(s1 / s0 + 1e-12)) < 2e-5
+    for k, dl in enumerate((0.5, 1.0, 2.0)):
+        sk = np.abs(a + dl - lam).min()
+        assert abs(g[20 + k] - np.log10(st[2] / sk)) < 2e-5
+
+
+def test_point_features_match_numpy():
+    b, kl, ku = inputs.grcar(120)
+    ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 23, 17)
+    x = restriction.point_features(ctx, grid).float().cpu().numpy()
+    idx = torch.as_tensor(np.array([5, 77, 390], dtype=np.int32), device=DEV)
+    xi = restriction.point_features(ctx, grid, idx).float().cpu().numpy()
+    np.testing.assert_array_equal(xi, x[[5, 77, 390]])
+    st = ctx.stats.cpu().numpy()
+    sym = ctx.symbol.cpu().numpy()
+    cen = st[0] + 1j * st[1]
+    R = st[2]
+    xs = grid.re_min + np.arange(grid.nx) * (4.0 / 22)
+    ys = grid.im_min + np.arange(grid.ny) * (7.0 / 16)
+    for f in (0, 5, 77, 200, 390):
+        i, j = divmod(f, grid.nx)
+        z = xs[j] + 1j * ys[i]
+        cx, cy = (xs[j] - 1.0) / 2.0, ys[i] / 3.5
+        ref = [cx, cy]
+        for k in range(1, 7):
+            w = 2 ** k
+            ref += [np.sin(w * cx), np.sin(w * cy), np.cos(w * cx), np.cos(w * cy)]
+        d = np.abs(sym - z)
+        ang = np.angle(np.roll(sym - z, -1) / (sym - z)).sum()
+        ref += [d.min() / R, abs(z - cen) / R, d.mean() / R, np.log10(d.min() / R + 1e-7),
+                np.log10(d.mean() / R + 1e-7), np.rint(ang / (2 * np.pi))]
+        # BF16 rows: 8 significant bits
+        np.testing.assert_allclose(x[f, :32], np.array(ref), rtol=1e-2, atol=2e-2)
+        np.testing.assert_allclose(x[f, 32:32 + _native.GLOBAL_FEATURES], ctx.glob.cpu().numpy(), rtol=1e-2, atol=1e-3)
+        assert np.all(x[f, 32 + _native.GLOBAL_FEATURES:] == 0)
+
+
+def test_region_and_tile_list_match_numpy():
+    rng = np.random.default_rng(3)
+    grid = inputs.Grid(0.0, 1.0, 0.0, 1.0, 37, 29)
+    prob = rng.random((29, 37)).astype(np.float32) ** 6
+    pt = torch.as_tensor(prob.ravel(), device=DEV)
+    for tau, r in ((0.5, 2), (0.9, 1), (0.99, 0)):
+        m = restriction.region_mask(pt, grid, tau, r).cpu().numpy().astype(bool)
+        np.testing.assert_array_equal(m, restriction.dilate_np(prob >= tau, r))
+        lst = restriction.region_list(torch.as_tensor(m.astype(np.uint8), device=DEV), grid).cpu().numpy()
+        np.testing.assert_array_equal(lst, psa.tile_order(np.flatnonzero(m.ravel()), grid.nx))
+
+
+def test_hierarchical_map_is_masked_full_map():
+    b, kl, ku = inputs.grcar(100)
+    ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
+    r = restriction.Restriction(DEV, seed=1)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 42, 30)
+    full = r.predict(ctx, grid, hierarchical=False)
+    for tau in (0.2, 0.5, 0.8):
+        h = r.predict(ctx, grid, hierarchical=True, tau=tau)
+        torch.testing.assert_close(h, restriction.Restriction.hierarchical_mask(full, tau), rtol=0, atol=0)
+
+
+def test_small_end_to_end_pipeline():
+    rng = np.random.default_rng(0)
+    tr = inputs.restriction_matrices(48, seed=5, n_min=150, n_max=400, nx=16, ny=16)
+    va = inputs.restriction_matrices(6, seed=6, n_min=150, n_max=400, nx=48, ny=48)
+    r = restriction.Restriction(DEV, seed=2)
+    mats = [(_t(b), kl, ku) for b, kl, ku, _, _ in tr]
+    x, y, _ = r.build_training_set(mats, [g for *_, g, _ in tr], rng)
+    hist = r.train(x, y, rng, epochs=6, patience=3)
+    assert hist[-1]["val_loss"] < hist[0]["val_loss"] * 1.5 and min(h["val_acc"] for h in hist) > 0.5
+    vm = [(_t(b), kl, ku) for b, kl, ku, _, _ in va]
+    vctx = restriction.matrix_contexts(vm)
+    vg = [g for *_, g, _ in va]
+    truth = []
+    for (b, kl, ku), g in zip(vm, vg):
+        truth.append(psa.sigma_min(b, kl, ku, g).sigma.cpu().numpy())
+    cal = r.calibrate(vctx, vg, truth)
+    assert 0.0 < cal["tau"] < 1.0
+    # restricted run on a fresh matrix: sigma on R equals the full grid bitwise
+    b, kl, ku, g = inputs.restriction_test_matrix(n=600, kl=2, ku=4, nx=64, ny=48, seed=9)
+    bt = _t(b)
+    ctx = restriction.matrix_contexts([(bt, kl, ku)])[0]
+    full = psa.sigma_min(bt, kl, ku, g, eps=(restriction.EPS,))
+    out, mask, idx, tm = r.restricted(ctx, g, (restriction.EPS,))
+    m = mask.cpu().numpy().astype(bool).ravel()
+    np.testing.assert_array_equal(out.sigma.cpu().numpy().ravel()[m], full.sigma.cpu().numpy().ravel()[m])
+    assert np.all(out.status.cpu().numpy().ravel()[~m] == psa.PT_NOT_EVALUATED)
+    met = restriction.recall_metrics(full.sigma.cpu().numpy() <= restriction.EPS, m.reshape(g.ny, g.nx))
+    assert met["recall"] >= 0.9, met
