@@ -639,6 +639,67 @@ def run_restriction(args):
     return 0
 
 
+def run_classifier(args):
+    """The classifier's tensor-core kernels: the MLP forward over the 1024 x 1024
+    grid's feature rows, and one large BF16 GEMM (8192^3) for the kernel alone."""
+    import torch
+    from paper_2605_04550_gb300 import mlp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    g = torch.Generator(device=dev).manual_seed(0)
+    rows = 1 << 20
+    x = (torch.randn(rows, mlp.IN, device=dev, generator=g) * 0.5).to(torch.bfloat16)
+    theta = mlp.init_theta(0, dev)
+    nb = mlp.workspace_bytes(rows, False)
+    buf, ptr = mlp._aligned_buffer(nb, dev)
+    prob = torch.empty(rows, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        mlp.forward(theta, x, out=prob, workspace=(buf, ptr, nb))
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        mlp.forward(theta, x, out=prob, workspace=(buf, ptr, nb))
+    e1.record()
+    torch.cuda.synchronize(dev)
+    fwd_ms = e0.elapsed_time(e1) / args.steps
+    fwd_flops = 2.0 * rows * (mlp.IN * mlp.HIDDEN + 2 * mlp.HIDDEN * mlp.HIDDEN + mlp.HIDDEN)
+    M = N = K = 8192
+    A = (torch.randn(M, K, device=dev, generator=g)).to(torch.bfloat16)
+    B = (torch.randn(N, K, device=dev, generator=g)).to(torch.bfloat16)
+    for _ in range(args.warmup):
+        C = mlp.gemm_bf16(A, B)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        C = mlp.gemm_bf16(A, B)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    gemm_ms = e0.elapsed_time(e1) / args.steps
+    ref = (A[:64].float() @ B.float().T)
+    err = float((C[:64] - ref).abs().max().item() / ref.abs().max().item())
+    gemm_tf = 2.0 * M * N * K / (gemm_ms * 1e-3) / 1e12
+    line = {"workload": "classifier", "metric": "MLP forward rows/s (BF16 tensor cores, FP32 accumulate)",
+            "value": rows / (fwd_ms * 1e-3), "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fwd_ms, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": f"MLP {mlp_desc()} over {rows} feature rows (one 1024x1024 grid)"},
+            "roofline": {"bound": "tensor", "achieved": fwd_flops / (fwd_ms * 1e-3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms * 1e-3) / 1e12 / peak, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"},
+            "gemm_8192": {"ms": gemm_ms, "tflops": gemm_tf, "frac_of_bf16_peak": gemm_tf / peak,
+                          "max_rel_err_vs_fp32": err}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def mlp_desc():
     return "128->256->256->256->1 (SiLU)"
 
@@ -653,7 +714,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--case", default="mid", choices=["mid", "small"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures")
-    ap.add_argument("--workload", default="grid", choices=["grid", "differentiation", "batched", "restriction"],
+    ap.add_argument("--workload", default="grid",
+                    choices=["grid", "differentiation", "batched", "restriction", "classifier"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
                          "batched: 256 matrices on their own grids; restriction: the learned restriction")
     ap.add_argument("--batch-size", type=int, default=256, help="batched: number of matrices")
@@ -673,6 +735,8 @@ def main():
         return run_batched(args)
     if args.workload == "restriction":
         return run_restriction(args)
+    if args.workload == "classifier":
+        return run_classifier(args)
     return run_gpu(args)
 
 

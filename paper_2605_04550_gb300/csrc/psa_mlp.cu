@@ -8,11 +8,12 @@
 //
 // GEMM: C[M x N] = A[M x K] * B[N x K]^T, A and B row-major BF16 (K contiguous,
 // "K-major"). One CTA of 128 threads computes a 128 x 128 tile of C: per K
-// chunk of 64 the four warps copy the A and B tiles into shared memory in the
-// core-matrix layout (8 rows x 16 bytes per core matrix, the 8 core matrices of
-// a row group consecutive along K), one thread issues four 128 x 128 x 16
-// MMAs into a 128-column FP32 accumulator in tensor memory and commits them to
-// an mbarrier, and the CTA waits on it before the next chunk. The epilogue
+// chunk of 64 the four warps copy the A and B tiles into one of two shared-
+// memory stages in the core-matrix layout (8 rows x 16 bytes per core matrix,
+// the 8 core matrices of a row group consecutive along K), one thread issues
+// four 128 x 128 x 16 MMAs into a 128-column FP32 accumulator in tensor memory
+// and commits them to that stage's mbarrier; the copy of the next chunk into
+// the other stage overlaps them. The epilogue
 // reads the accumulator with tcgen05.ld (warp w owns rows 32w .. 32w + 31),
 // adds the bias and writes any of: FP32 pre-activation, BF16 SiLU output,
 // BF16 SiLU output transposed (for the weight-gradient GEMMs of training).
@@ -45,7 +46,9 @@ static_assert(NPARAM == PSA_MLP_PARAMS, "parameter count");
 constexpr int TILE = 128;       // M and N of a CTA tile
 constexpr int KCH = 64;         // K per shared-memory chunk (4 MMAs of K = 16)
 constexpr int TILE_BYTES = TILE * KCH * 2;
-constexpr int GEMM_SMEM = 48 * 1024;  // A tile, B tile, barrier; 48 KB keeps <= 4 CTAs (512 TMEM columns) per SM
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B tiles of one K chunk
+// two stages, barriers and the TMEM slot; 72 KB keeps <= 3 CTAs (384 TMEM columns) per SM
+constexpr int GEMM_SMEM = 72 * 1024;
 constexpr int WAIT_LIMIT = 1 << 20;
 constexpr int64_t FWD_CHUNK = 131072;  // rows per forward pass through the workspace
 
@@ -75,16 +78,16 @@ __device__ __forceinline__ int core_off(int row, int k)
 __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *const sA = smem;
-    unsigned char *const sB = smem + TILE_BYTES;
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + 2 * TILE_BYTES);
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(smem + 2 * TILE_BYTES + 8);
+    // two stages of (A tile, B tile), then one mbarrier per stage and the TMEM slot
+    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE_BYTES);
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE_BYTES + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TILE, n0 = blockIdx.y * TILE;
 
     if (warp == 0) tc::tmem_alloc(tslot, TILE);
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
@@ -92,11 +95,28 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE, TILE);
-    const uint32_t a_base = tc::smem_addr(sA), b_base = tc::smem_addr(sB);
+    const uint32_t s_base = tc::smem_addr(smem);
 
+    // K chunk c goes to stage c & 1: its tiles are written while the tensor core still
+    // works on chunk c - 1 from the other stage; before chunk c overwrites a stage, the
+    // MMAs of chunk c - 2 that read it must have completed (that stage's barrier).
     bool ok = true;
-    uint32_t phase = 0;
-    for (int k0 = 0; k0 < g.K; k0 += KCH) {
+    uint32_t phase[2] = {0u, 0u};
+    const int nk = g.K / KCH;
+    for (int c = 0; c < nk && ok; ++c) {
+        const int st = c & 1;
+        if (c >= 2) {
+            bool done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
+            if (!done) done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
+            if (!__syncthreads_and(done ? 1 : 0)) {
+                ok = false;
+                break;
+            }
+            phase[st] ^= 1u;
+        }
+        unsigned char *const sA = smem + st * STAGE_BYTES;
+        unsigned char *const sB = sA + TILE_BYTES;
+        const int k0 = c * KCH;
         // 128 rows x 64 columns = 1024 vectors of 8 BF16 per operand
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -112,24 +132,23 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
+            const uint32_t a_base = s_base + st * STAGE_BYTES, b_base = a_base + TILE_BYTES;
 #pragma unroll
             for (int s = 0; s < KCH / 16; ++s) {
                 // K step s covers core matrices 2s and 2s + 1 of every row group
                 const uint64_t ad = tc::smem_desc(a_base + s * 256, 128, (KCH / 8) * 128);
                 const uint64_t bd = tc::smem_desc(b_base + s * 256, 128, (KCH / 8) * 128);
-                tc::mma_bf16(tmem, ad, bd, IDESC, (k0 > 0 || s > 0) ? 1u : 0u);
+                tc::mma_bf16(tmem, ad, bd, IDESC, (c > 0 || s > 0) ? 1u : 0u);
             }
-            tc::mma_commit(bar);
+            tc::mma_commit(&bar[st]);
         }
-        // the MMAs have read the tiles (and written the accumulator) once the phase
-        // completes; the CTA leaves the loop together if any thread's wait ran out
-        bool done = tc::mbar_wait(bar, phase, WAIT_LIMIT);
-        if (!done) done = tc::mbar_wait(bar, phase, WAIT_LIMIT);  // in-flight MMAs get a second limit
-        if (!__syncthreads_and(done ? 1 : 0)) {
-            ok = false;
-            break;
-        }
-        phase ^= 1u;
+    }
+    // the last chunk's commit covers every MMA issued before it
+    if (ok && nk > 0) {
+        const int st = (nk - 1) & 1;
+        bool done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
+        if (!done) done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
     }
     tc::fence_after_sync();
 
