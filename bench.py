@@ -51,7 +51,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per Lanczos row-step of k_sigma_min<2,5>, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the reduced n = 256 case, see
 # profiles/k_sigma_min_toeplitz256_sections.md; traffic scales with row-steps
-DRAM_BYTES_PER_ROW_STEP = 537.0
+DRAM_BYTES_PER_ROW_STEP = 532.0
 
 
 # reduced case for profiler captures: same matrix family, n = 256, 384 x 384 grid
@@ -452,7 +452,7 @@ def run_batched(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     t0 = time.perf_counter()
     if args.no_tune:
-        best, tune = batch.BatchConfig(), {}
+        best, tune = batch.BatchConfig(streams=args.batch_streams), {}
     else:
         sub = batch.BatchPlan(mats[::32]) if len(mats) >= 64 else plan
         cands = [batch.BatchConfig(0, order, streams) for streams in (2, 4, 8)
@@ -725,6 +725,7 @@ def main():
     ap.add_argument("--restrict-test-n", type=int, default=20000, help="restriction: order of the test matrix")
     ap.add_argument("--restrict-grid", type=int, default=1024, help="restriction: test grid side")
     ap.add_argument("--no-tune", action="store_true", help="batched: default launch controls")
+    ap.add_argument("--batch-streams", type=int, default=8, help="batched with --no-tune: streams")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":
