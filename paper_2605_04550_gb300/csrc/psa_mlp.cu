@@ -7,20 +7,22 @@
 // optimiser run on the CUDA cores.
 //
 // GEMM: C[M x N] = A[M x K] * B[N x K]^T, A and B row-major BF16 (K contiguous,
-// "K-major"). One CTA of 128 threads computes a 128 x 128 tile of C: per K
-// chunk of 64 the four warps copy the A and B tiles into one of two shared-
-// memory stages in the core-matrix layout (8 rows x 16 bytes per core matrix,
-// the 8 core matrices of a row group consecutive along K), one thread issues
+// "K-major"). One CTA of 128 threads computes a 128 x 128 tile of C. Per K
+// chunk of 64, TMA copies the A and B tiles (128 rows x 128 bytes each) into one
+// of three shared-memory stages with the 128-byte swizzle; one thread issues
 // four 128 x 128 x 16 MMAs into a 128-column FP32 accumulator in tensor memory
-// and commits them to that stage's mbarrier; the copy of the next chunk into
-// the other stage overlaps them. The epilogue
+// once the stage's transaction barrier completes, commits them to the stage's
+// second barrier, and refills the stage of the previous chunk as soon as its
+// MMAs are done, so copies run two chunks ahead of the tensor core. The epilogue
 // reads the accumulator with tcgen05.ld (warp w owns rows 32w .. 32w + 31),
 // adds the bias and writes any of: FP32 pre-activation, BF16 SiLU output,
 // BF16 SiLU output transposed (for the weight-gradient GEMMs of training).
 #include <atomic>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <mutex>
 
 #include "psa.h"
 #include "psa_tc.cuh"
@@ -47,8 +49,10 @@ constexpr int TILE = 128;       // M and N of a CTA tile
 constexpr int KCH = 64;         // K per shared-memory chunk (4 MMAs of K = 16)
 constexpr int TILE_BYTES = TILE * KCH * 2;
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B tiles of one K chunk
-// two stages, barriers and the TMEM slot; 72 KB keeps <= 3 CTAs (384 TMEM columns) per SM
-constexpr int GEMM_SMEM = 72 * 1024;
+constexpr int STAGES = 3;
+// stages + barriers + TMEM slot + 1 KB for aligning the stages to the swizzle atom:
+// 98 KB keeps <= 2 CTAs (256 TMEM columns) per SM
+constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 2048;
 constexpr int WAIT_LIMIT = 1 << 20;
 constexpr int64_t FWD_CHUNK = 131072;  // rows per forward pass through the workspace
 
@@ -69,25 +73,27 @@ struct GemmArgs {
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 
-// Byte offset of element (row, k) of a 128 x 64 tile in the core-matrix layout.
-__device__ __forceinline__ int core_off(int row, int k)
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+                                                   const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
 {
-    return (((row >> 3) * (KCH / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
-}
-
-__global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    // two stages of (A tile, B tile), then one mbarrier per stage and the TMEM slot
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE_BYTES);
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE_BYTES + 16);
+    extern __shared__ unsigned char smem_raw[];
+    // stages of (A tile, B tile) on 1024-byte boundaries (the swizzle atom), then the
+    // barriers and the TMEM slot
+    unsigned char *const smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *const full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *const empty = full + STAGES;
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(empty + STAGES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TILE, n0 = blockIdx.y * TILE;
+    const int nk = g.K / KCH;
 
     if (warp == 0) tc::tmem_alloc(tslot, TILE);
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
@@ -95,60 +101,54 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE, TILE);
-    const uint32_t s_base = tc::smem_addr(smem);
 
-    // K chunk c goes to stage c & 1: its tiles are written while the tensor core still
-    // works on chunk c - 1 from the other stage; before chunk c overwrites a stage, the
-    // MMAs of chunk c - 2 that read it must have completed (that stage's barrier).
+    // Thread 0 runs the pipeline: TMA loads of K chunk c into stage c % STAGES
+    // complete on full[stage]; the chunk's four MMAs commit to empty[stage]; a stage is
+    // loaded again once the MMAs that read it have completed.
     bool ok = true;
-    uint32_t phase[2] = {0u, 0u};
-    const int nk = g.K / KCH;
-    for (int c = 0; c < nk && ok; ++c) {
-        const int st = c & 1;
-        if (c >= 2) {
-            bool done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
-            if (!done) done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
-            if (!__syncthreads_and(done ? 1 : 0)) {
+    if (tid == 0) {
+        auto issue = [&](int c) {
+            unsigned char *const sA = smem + (c % STAGES) * STAGE_BYTES;
+            tc::mbar_arrive_expect_tx(&full[c % STAGES], STAGE_BYTES);
+            tc::tma_load_2d(sA, &tmA, c * KCH, m0, &full[c % STAGES]);
+            tc::tma_load_2d(sA + TILE_BYTES, &tmB, c * KCH, n0, &full[c % STAGES]);
+        };
+        for (int c = 0; c < nk && c < STAGES; ++c) issue(c);
+        for (int c = 0; c < nk && ok; ++c) {
+            const int st = c % STAGES;
+            const uint32_t par = (uint32_t)((c / STAGES) & 1);
+            if (!tc::mbar_wait(&full[st], par, WAIT_LIMIT)) {
                 ok = false;
                 break;
             }
-            phase[st] ^= 1u;
-        }
-        unsigned char *const sA = smem + st * STAGE_BYTES;
-        unsigned char *const sB = sA + TILE_BYTES;
-        const int k0 = c * KCH;
-        // 128 rows x 64 columns = 1024 vectors of 8 BF16 per operand
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int v = tid + 128 * i;
-            const int row = v >> 3, kc = (v & 7) * 8;
-            uint4 a = make_uint4(0u, 0u, 0u, 0u);
-            if (m0 + row < g.M) a = *reinterpret_cast<const uint4 *>(g.A + (int64_t)(m0 + row) * g.lda + k0 + kc);
-            *reinterpret_cast<uint4 *>(sA + core_off(row, kc)) = a;
-            const uint4 b = *reinterpret_cast<const uint4 *>(g.B + (int64_t)(n0 + row) * g.ldb + k0 + kc);
-            *reinterpret_cast<uint4 *>(sB + core_off(row, kc)) = b;
-        }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a_base = s_base + st * STAGE_BYTES, b_base = a_base + TILE_BYTES;
+            const uint32_t a_base = tc::smem_addr(smem + st * STAGE_BYTES), b_base = a_base + TILE_BYTES;
 #pragma unroll
-            for (int s = 0; s < KCH / 16; ++s) {
-                // K step s covers core matrices 2s and 2s + 1 of every row group
-                const uint64_t ad = tc::smem_desc(a_base + s * 256, 128, (KCH / 8) * 128);
-                const uint64_t bd = tc::smem_desc(b_base + s * 256, 128, (KCH / 8) * 128);
-                tc::mma_bf16(tmem, ad, bd, IDESC, (c > 0 || s > 0) ? 1u : 0u);
+            for (int s = 0; s < KCH / 16; ++s)
+                tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + s * 32), tc::smem_desc_sw128(b_base + s * 32), IDESC,
+                             (c > 0 || s > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[st]);
+            // refill the stage of chunk c - 1 (its MMAs are queued ahead of chunk c's)
+            const int r = c - 1 + STAGES;
+            if (c >= 1 && r < nk) {
+                const int sp = (c - 1) % STAGES;
+                if (!tc::mbar_wait(&empty[sp], (uint32_t)(((c - 1) / STAGES) & 1), WAIT_LIMIT)) {
+                    ok = false;
+                    break;
+                }
+                issue(r);
             }
-            tc::mma_commit(&bar[st]);
         }
     }
-    // the last chunk's commit covers every MMA issued before it
-    if (ok && nk > 0) {
-        const int st = (nk - 1) & 1;
-        bool done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
-        if (!done) done = tc::mbar_wait(&bar[st], phase[st], WAIT_LIMIT);
-        ok = __syncthreads_and(done ? 1 : 0) != 0;
+    // everyone waits for the last chunk's commit, which covers every MMA issued before it
+    {
+        const int last = nk - 1;
+        bool done = true;
+        if (last >= 0) {
+            done = tc::mbar_wait(&empty[last % STAGES], (uint32_t)((last / STAGES) & 1), WAIT_LIMIT);
+            if (!done) done = tc::mbar_wait(&empty[last % STAGES], (uint32_t)((last / STAGES) & 1), WAIT_LIMIT);
+        }
+        ok = __syncthreads_and((done && ok) ? 1 : 0) != 0;
     }
     tc::fence_after_sync();
 
@@ -184,6 +184,43 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g)
 constexpr int kMaxDevices = 64;
 std::atomic<bool> g_attr_set[kMaxDevices];
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::once_flag g_encode_once;
+EncodeTiledFn g_encode = nullptr;
+
+EncodeTiledFn encode_fn()
+{
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    });
+    return g_encode;
+}
+
+// Tensor map of a row-major BF16 matrix [rows][cols] (leading dimension ld elements)
+// read in 128 x 64 boxes with the 128-byte swizzle; rows past the end read as zero.
+cudaError_t tile_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, int64_t cols, int64_t ld)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)TILE};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
 {
     // the dynamic shared-memory limit is a per-device attribute of the kernel
@@ -196,8 +233,11 @@ cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
         if (e != cudaSuccess) return e;
         g_attr_set[dev].store(true);
     }
+    CUtensorMap ta, tb;
+    if ((e = tile_map(&ta, g.A, g.M, g.K, g.lda)) != cudaSuccess) return e;
+    if ((e = tile_map(&tb, g.B, g.N, g.K, g.ldb)) != cudaSuccess) return e;
     const dim3 grid((unsigned)((g.M + TILE - 1) / TILE), (unsigned)(g.N / TILE));
-    k_gemm_bf16<<<grid, 128, GEMM_SMEM, s>>>(g);
+    k_gemm_bf16<<<grid, 128, GEMM_SMEM, s>>>(ta, tb, g);
     return cudaGetLastError();
 }
 

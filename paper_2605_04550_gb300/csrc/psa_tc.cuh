@@ -84,14 +84,36 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// Shared-memory matrix descriptor, no swizzle, K-major operand made of 8-row x
-// 16-byte core matrices: lbo = byte distance between core matrices along K,
-// sbo = byte distance between 8-row groups along M (or N); bits 46..47 hold the
-// descriptor version (1) that tcgen05 requires.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
+// layout that a TMA tile load with CU_TENSOR_MAP_SWIZZLE_128B writes (rows of 64
+// BF16, 8-row atoms of 1024 bytes): start address / 16 at bits 0..13, lbo unused
+// (encoded 1) at 16..29, sbo = 1024 / 16 at 32..45, descriptor version 1 at 46..47
+// (required by tcgen05), layout type 2 (128-byte swizzle) at 61..63. The tile base
+// must be 1024-byte aligned; a K step of 16 elements inside the row advances the
+// start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// The barrier expects `bytes` more transaction bytes in the current phase (and this
+// thread's arrival).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: 2D tile load of the tensor map's box at (c0 = inner coordinate, c1 = row)
+// into shared memory, completing `bytes` on the barrier.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
 }
 
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an F32
