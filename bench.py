@@ -81,6 +81,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over the ranks of the process group (the job's time is the
+    slowest replica's); the value itself when no group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world_size: int, units_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput of replicas: every rank does the same units per step;
+    the job takes the slowest rank's time."""
+    return world_size * units_per_rank_step * steps / (max_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -253,13 +272,8 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    dev_ms = float(np.sum(step_ms))
-    if ws_ > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    value = ws_ * npts * args.steps / (dev_ms * 1e-3)
+    dev_ms = max_over_ranks(float(np.sum(step_ms)), dev)
+    value = job_rate(ws_, npts, args.steps, dev_ms)
 
     steps = out.steps.cpu().numpy().ravel()
     status = out.status.cpu().numpy().ravel()
