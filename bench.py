@@ -54,6 +54,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 DRAM_BYTES_PER_ROW_STEP = 532.0
 
 
+# the classifier trained by `bench.py --workload restriction --save-model ...`
+MODEL_PATH = os.path.join(ROOT, "paper_2605_04550_gb300", "data", "restriction_mlp.npz")
+
 # reduced case for profiler captures: same matrix family, n = 256, 384 x 384 grid
 # (about 2.5 waves of points in flight), k_max 300 -> about 3.5 GB of workspace
 SMALL = dict(n=256, nx=384, ny=384, kmax=300)
@@ -341,6 +344,29 @@ def run_gpu(args):
                   "coverage": coverage, "full_ms": mean_ms, "restricted_ms": r_ms,
                   "speedup": mean_ms / r_ms if r_ms > 0 else None, "sigma_bitwise_equal_on_region": same}
 
+    # ---------------- the same with the learned classifier's region (trained weights shipped
+    # with the package: bench.py --workload restriction --save-model ...)
+    restricted_learned = None
+    if os.path.exists(MODEL_PATH):
+        from paper_2605_04550_gb300 import restriction as rst
+        model = rst.Restriction.load(MODEL_PATH, dev)
+        flush.fill_(-2.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx = rst.matrix_contexts([(b_dev, kl, ku)], model.eps)[0]
+        torch.cuda.synchronize(dev)
+        feat_ms = (time.perf_counter() - t0) * 1e3
+        out_l, mask_l, idx_l, tm = model.restricted(ctx, grid, EPS, opts=opts, workspace=wsp)
+        m_l = mask_l.cpu().numpy().astype(bool)
+        met = rst.recall_metrics(sig <= model.eps, m_l)
+        hyb = feat_ms + tm["nn_ms"] + tm["restricted_ms"]
+        restricted_learned = {"eps": model.eps, "tau": model.tau, "model": os.path.relpath(MODEL_PATH, ROOT),
+                              "features_ms": feat_ms, "nn_ms": tm["nn_ms"], "restricted_ms": tm["restricted_ms"],
+                              "full_ms": mean_ms, "speedup_actual": mean_ms / hyb,
+                              "speedup_best": mean_ms / tm["restricted_ms"], "region_points": int(idx_l.numel()),
+                              **met, "sigma_bitwise_equal_on_region":
+                                  bool(np.array_equal(out_l.sigma.cpu().numpy()[m_l], sig[m_l]))}
+
     probe = psa.probe_dfma_rate(4096)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
@@ -370,6 +396,7 @@ def run_gpu(args):
         "lane_utilisation": lane_util,
         "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
         "restricted": restricted,
+        "restricted_learned": restricted_learned,
         "wall_s_timed": wall,
     }
     if rank == 0 and not args.no_cpu:
@@ -649,6 +676,11 @@ def run_restriction(args):
             "pipeline_seconds": {"labels_and_features": t_labels, "training": t_train, "calibration": t_cal,
                                  "total": time.perf_counter() - t_all, "training_set": model.timing},
             "clocks": clk.summary(), "gpu_launches": None}
+    if args.save_model:
+        model.save(args.save_model, meta={"training_matrices": args.restrict_train,
+                                          "validation_matrices": args.restrict_val,
+                                          "validation_grid": args.restrict_val_grid, "seed_train": 1,
+                                          "seed_val": 2, "label_tol": restriction.LABEL_OPTS.tol})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -738,6 +770,7 @@ def main():
     ap.add_argument("--restrict-val-grid", type=int, default=128, help="restriction: validation grid side")
     ap.add_argument("--restrict-test-n", type=int, default=20000, help="restriction: order of the test matrix")
     ap.add_argument("--restrict-grid", type=int, default=1024, help="restriction: test grid side")
+    ap.add_argument("--save-model", default=None, help="restriction: write the trained classifier (.npz)")
     ap.add_argument("--no-tune", action="store_true", help="batched: default launch controls")
     ap.add_argument("--batch-streams", type=int, default=8, help="batched with --no-tune: streams")
     args = ap.parse_args()

@@ -186,6 +186,31 @@ class Restriction:
         self.history = []
         self.calibration = {}
 
+    # ---------------------------------------------------------- persistence
+    def save(self, path: str, meta: Optional[dict] = None):
+        """Parameters, threshold and calibration summary to an .npz file."""
+        import json
+        th = self.theta.detach().cpu().numpy().astype(np.float32)
+        info = {"tau": self.tau, "eps": self.eps, "meta": meta or {},
+                "calibration": {k: v for k, v in self.calibration.items() if k != "table"}}
+        np.savez(path, theta=th, info=np.frombuffer(json.dumps(info).encode(), dtype=np.uint8))
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        import json
+        import torch
+        d = np.load(path)
+        th = d["theta"]
+        if th.shape != (mlp.NPARAM,) or th.dtype != np.float32:
+            raise ValueError("parameter vector of the wrong size")
+        info = json.loads(bytes(d["info"]).decode())
+        r = cls(device, eps=float(info["eps"]))
+        r.theta = torch.as_tensor(th, device=device)
+        r.tau = float(info["tau"])
+        r.calibration = info.get("calibration", {})
+        r.meta = info.get("meta", {})
+        return r
+
     # ------------------------------------------------------------ training
     def build_training_set(self, mats, grids, rng: np.random.Generator, opts: LanczosOpts = LABEL_OPTS):
         """Features and labels of the training matrices, balanced per matrix: all
