@@ -155,5 +155,27 @@ def test_small_end_to_end_pipeline():
     m = mask.cpu().numpy().astype(bool).ravel()
     np.testing.assert_array_equal(out.sigma.cpu().numpy().ravel()[m], full.sigma.cpu().numpy().ravel()[m])
     assert np.all(out.status.cpu().numpy().ravel()[~m] == psa.PT_NOT_EVALUATED)
+    # a network trained on 48 small matrices for a few epochs (the weights depend on the
+    # order of atomic gradient sums) is only checked for doing better than chance here;
+    # the recall bar is on the shipped classifier below
     met = restriction.recall_metrics(full.sigma.cpu().numpy() <= restriction.EPS, m.reshape(g.ny, g.nx))
-    assert met["recall"] >= 0.9, met
+    assert met["recall"] >= 0.5, met
+
+
+def test_shipped_classifier_reaches_recall_on_a_fresh_matrix():
+    """The classifier shipped with the package (trained on 2000 seeded matrices) on a
+    matrix outside its training set: recall against the 3x3-dilated truth >= 0.99,
+    sigma on the region bitwise equal to the full grid."""
+    import os
+    path = os.path.join(os.path.dirname(restriction.__file__), "data", "restriction_mlp.npz")
+    r = restriction.Restriction.load(path, DEV)
+    for n, kl, ku, nx, ny, seed in ((600, 2, 4, 64, 48, 9), (1500, 3, 6, 96, 80, 31)):
+        b, kl, ku, g = inputs.restriction_test_matrix(n=n, kl=kl, ku=ku, nx=nx, ny=ny, seed=seed)
+        bt = _t(b)
+        ctx = restriction.matrix_contexts([(bt, kl, ku)])[0]
+        full = psa.sigma_min(bt, kl, ku, g, eps=(restriction.EPS,))
+        out, mask, idx, tm = r.restricted(ctx, g, (restriction.EPS,))
+        m = mask.cpu().numpy().astype(bool)
+        np.testing.assert_array_equal(out.sigma.cpu().numpy()[m], full.sigma.cpu().numpy()[m])
+        met = restriction.recall_metrics(full.sigma.cpu().numpy() <= restriction.EPS, m)
+        assert met["recall"] >= 0.99, (n, met)
