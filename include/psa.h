@@ -325,8 +325,9 @@ int psa_batch_workspace_bytes(const void *plan_host, const psa_lanczos_opts *opt
  *  aux_streams, n_aux  0 to 7 further cudaStream_t, all different from each
  *                   other and from stream (n_aux = 0: every class on stream).
  * Errors: PSA_EINVAL (bad eps, opts or order, a plan whose header does not
- * check, n_aux out of range, a repeated stream), PSA_EWORKSPACE (no room for
- * one warp in some class), PSA_ECUDA. */
+ * check, n_aux out of range, a repeated stream), PSA_EUNSUPPORTED (a class of
+ * more than 65535 matrices), PSA_EWORKSPACE (no room for one warp in some
+ * class), PSA_ECUDA. */
 int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const double *eps, int32_t n_eps,
                           double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
                           const psa_lanczos_opts *opts, int64_t points_in_flight, int32_t order,

@@ -770,6 +770,7 @@ int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const dou
         if (pc.kl < 0 || pc.kl > kMaxKL || pc.ku < 0 || pc.ku > kMaxKU || pc.count < 1 || pc.ngroups < 1 ||
             pc.first < 0 || pc.first + pc.count > H.nmat || pc.ngroups > H.max_ngroups)
             return PSA_EINVAL;
+        if (pc.count > 65535) return PSA_EUNSUPPORTED;  // one grid row of the input check per matrix
         ClassRun &r = run[c];
         r.ops = pick_ops(pc.kl, pc.ku);
         if (!r.ops.launch) return PSA_EUNSUPPORTED;
