@@ -45,9 +45,11 @@ def check_sigma(sigma, ref, norm1, rel=REL, abs_=ABS):
     bound = rel * ref + abs_ * norm1
     err = np.abs(sigma - ref)
     bad = ~(err <= bound)
+    well = (ref >= 1e-3 * norm1) & (ref > 0)
+    floor = ref < 1e-3 * norm1
     info = {
-        "max_rel_well": float((err / ref)[ref >= 1e-3 * norm1].max()) if np.any(ref >= 1e-3 * norm1) else 0.0,
-        "max_abs_floor": float((err / norm1)[ref < 1e-3 * norm1].max()) if np.any(ref < 1e-3 * norm1) else 0.0,
+        "max_rel_well": float((err[well] / ref[well]).max()) if np.any(well) else 0.0,
+        "max_abs_floor": float((err[floor] / norm1[floor]).max()) if np.any(floor) else 0.0,
         "below_floor": int(np.sum((sigma <= abs_ * norm1) & (ref <= abs_ * norm1))),
         "n_bad": int(bad.sum()),
     }
