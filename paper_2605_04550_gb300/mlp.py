@@ -82,6 +82,8 @@ def forward(theta, x, out=None, workspace=None, stream=None):
     if theta.dtype != torch.float32 or theta.numel() != NPARAM or not theta.is_contiguous():
         raise ValueError("theta must be a contiguous float32 vector of the parameter count")
     prob = out if out is not None else torch.empty(rows, dtype=torch.float32, device=x.device)
+    if prob.dtype != torch.float32 or not prob.is_contiguous() or prob.numel() < rows or prob.device != x.device:
+        raise ValueError("out must be a contiguous float32 tensor of at least `rows` values on x's device")
     if workspace is None:
         nb = workspace_bytes(rows, False)
         buf, ptr = _aligned_buffer(nb, x.device)

@@ -99,9 +99,15 @@ def point_features(ctx: MatrixContext, grid: Grid, idx=None, out=None):
     dev = ctx.bands.device
     n = grid.npoints if idx is None else int(idx.numel())
     x = out if out is not None else torch.empty((n, mlp.IN), dtype=torch.bfloat16, device=dev)
+    if n == 0:
+        return x  # an empty list (a NULL list would mean the full grid)
+    if idx is not None and (idx.dtype != torch.int32 or not idx.is_contiguous() or idx.device != dev):
+        raise TypeError("idx must be a contiguous int32 tensor on the bands' device")
+    if x.shape != (n, mlp.IN) or x.dtype != torch.bfloat16 or not x.is_contiguous():
+        raise ValueError("out must be a contiguous bfloat16 (npoints, IN) tensor")
     g = _grid_c(grid)
     s = torch.cuda.current_stream(dev)
-    _native.check(lib.psa_point_features(ctypes.byref(g), idx.data_ptr() if idx is not None and n else None,
+    _native.check(lib.psa_point_features(ctypes.byref(g), idx.data_ptr() if idx is not None else None,
                                          n if idx is not None else 0, ctx.stats.data_ptr(), ctx.symbol.data_ptr(),
                                          ctx.glob.data_ptr(), x.data_ptr(), s.cuda_stream), "psa_point_features")
     return x
@@ -111,6 +117,8 @@ def region_mask(prob, grid: Grid, tau: float, radius: int = 2):
     """uint8 (ny, nx): dilate_{(2 radius + 1)^2}({p >= tau})."""
     import torch
     lib = _native.load()
+    if prob.dtype != torch.float32 or not prob.is_cuda or not prob.is_contiguous() or prob.numel() != grid.npoints:
+        raise ValueError("prob must be a contiguous CUDA float32 tensor with one value per grid point")
     out = torch.empty((grid.ny, grid.nx), dtype=torch.uint8, device=prob.device)
     _native.check(lib.psa_region(prob.data_ptr(), float(tau), grid.nx, grid.ny, int(radius), out.data_ptr(),
                                  torch.cuda.current_stream(prob.device).cuda_stream), "psa_region")
@@ -121,6 +129,8 @@ def region_list(mask, grid: Grid):
     """Flat indices (CUDA int32) of a mask's points in tile order (the restricted list)."""
     import torch
     lib = _native.load()
+    if mask.dtype != torch.uint8 or not mask.is_cuda or not mask.is_contiguous() or mask.numel() != grid.npoints:
+        raise ValueError("mask must be a contiguous CUDA uint8 tensor with one value per grid point")
     slots = torch.empty(((grid.nx + 7) // 8) * ((grid.ny + 3) // 4) * 32, dtype=torch.int32, device=mask.device)
     _native.check(lib.psa_tile_slots(mask.data_ptr(), grid.nx, grid.ny, slots.data_ptr(),
                                      torch.cuda.current_stream(mask.device).cuda_stream), "psa_tile_slots")
