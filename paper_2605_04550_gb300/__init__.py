@@ -112,6 +112,15 @@ class Workspace:
 
 
 
+def _check_out(out, npoints: int, dev) -> None:
+    """Caller-provided outputs: contiguous, on the device, one entry per grid point."""
+    import torch
+    for t, dt, name in ((out.sigma, torch.float64, "sigma"), (out.mask, torch.int32, "mask"),
+                        (out.status, torch.int8, "status"), (out.steps, torch.int32, "steps")):
+        if t.dtype != dt or t.device != dev or not t.is_contiguous() or t.numel() != npoints:
+            raise ValueError(f"out.{name} must be a contiguous {dt} tensor of {npoints} entries on {dev}")
+
+
 def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), idx=None,
               opts: Optional[LanczosOpts] = None, workspace: Optional[Workspace] = None,
               points_in_flight: Optional[int] = None, out: Optional[SigmaMinResult] = None,
@@ -145,6 +154,8 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
                              torch.empty(shape, dtype=torch.int32, device=dev),
                              torch.empty(shape, dtype=torch.int8, device=dev),
                              torch.empty(shape, dtype=torch.int32, device=dev))
+    else:
+        _check_out(out, grid.npoints, dev)
     eps_arr = (ctypes.c_double * max(len(eps), 1))(*[float(e) for e in eps])
     idx_ptr = None
     if idx is not None:

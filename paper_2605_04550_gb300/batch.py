@@ -174,6 +174,9 @@ def sigma_min_batched(plan: BatchPlan, eps: Sequence[float] = (), opts: Optional
         N = plan.npoints
         out = BatchResult(torch.empty(N, dtype=torch.float64, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
                           torch.empty(N, dtype=torch.int8, device=dev), torch.empty(N, dtype=torch.int32, device=dev))
+    else:
+        from . import _check_out
+        _check_out(out, plan.npoints, dev)
     eps_arr = (ctypes.c_double * max(len(eps), 1))(*[float(e) for e in eps])
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     if not 1 <= config.streams <= MAX_STREAMS:
