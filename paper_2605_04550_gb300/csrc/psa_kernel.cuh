@@ -612,65 +612,89 @@ for (int j = 0; j < (bad_input ? 0 : n); ++j) {
 #undef PIVOF
 }
 
-// Lanczos on H' = (B B^*)^{-1} / 2^(2 e1) for the point held by this lane, after
-// band_lu: steps until the stopping test, beta = 0 or k_max. Returns the point's
-// status (0 OK, 2 NOT_CONVERGED, 5 UNDERFLOW) and sets sigma, the steps taken, the
-// final Ritz value theta (in H' units) and the Lanczos scalars st.
+// The Lanczos process of one point (the lane's), advanced one step at a time.
+struct LzRun {
+    LzState st;
+    double theta = 0.0, theta_prev = 0.0, dprev = 0.0;
+    int k = 0;       // steps taken
+    int kth = 0;     // step whose Ritz value `theta` holds
+    int ksteps = 0;  // steps that produced a Ritz value
+};
+
+// Step k + 1 of the Lanczos process on H' = (B B^*)^{-1} / 2^(2 e1) after band_lu, with
+// the Ritz value and the stopping test. Returns -1 to go on, else the point's status:
+// 0 converged (or beta = 0: the Krylov space is exhausted), 2 k_max reached without
+// meeting the test, 5 a value left the double range.
 template <int KL, int KU>
-__device__ __forceinline__ int lanczos_sigma(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
-                                             double *const Ta, double *const Tb, LzState &st, double &sigma, int &ksteps,
-                                             double &theta)
+__device__ __forceinline__ int lz_advance(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
+                                          double *const Ta, double *const Tb, LzRun &r)
 {
     constexpr int64_t TS = 32;
-    int status;
-    // ---------------- 2. Lanczos on H'
     // The stored Lanczos vectors are v_k = u_k = beta_{k-1} q_k (v_1 = q_1), not
     // normalised: 1/beta rides on the scalars of the next sweep. 2^e1 is the
     // binary exponent of the largest component of B^{-1} q_1 (about 1/sigma);
     // for |e1| <= 450 the solves of later steps stay inside the double range
     // (x ~ beta 2^e1, y ~ beta 2^(2 e1) theta') and need no rescaling.
-    double theta_prev = 0.0, dprev = 0.0;
-    theta = 0.0;
-    sigma = 0.0;
-    ksteps = 0;
-    int kth = 0;  // step whose Ritz value `theta` holds
     const int kmax = p.k_max;
     const int kr0 = max(1, min(p.k_min, kmax) - 1);  // first step whose Ritz value is needed
     const int kc0 = max(2, p.k_min);                 // first step with a stopping test
-    status = 2;  // NOT_CONVERGED
-    for (int k = 1;; ++k) {
-        double alpha = 0.0;
-        const int rs = lanczos_step<KL, KU, false>(p, M, rows, pivs, Ta, Tb, k, st, alpha, 0.0, false);
-        if (rs >= 0) { status = rs; break; }
-        ksteps = k;
-
-        // ---------------- 3. Ritz value and stopping test
-        if (k >= kr0) {
-            double th;
-            if (k == 1) th = alpha;
-            else if (kth == k - 1) th = ritz_top(Ta, Tb, TS, k, theta, dprev, alpha, st.beta_p * st.beta_p);
-            else th = ritz_top_cold(Ta, Tb, TS, k);
-            const bool have_prev = (kth == k - 1);
-            theta_prev = theta;
-            theta = th;
-            kth = k;
-            dprev = have_prev ? theta - theta_prev : 0.0;
-            if (k >= kc0 && have_prev && theta - theta_prev <= p.tol * theta) { status = 0; break; }
-        }
-        if (k >= kmax) break;
+    const int k = r.k + 1;
+    double alpha = 0.0;
+    const int rs = lanczos_step<KL, KU, false>(p, M, rows, pivs, Ta, Tb, k, r.st, alpha, 0.0, false);
+    r.k = k;
+    if (rs >= 0) return rs;
+    r.ksteps = k;
+    if (k >= kr0) {
+        double th;
+        if (k == 1) th = alpha;
+        else if (r.kth == k - 1) th = ritz_top(Ta, Tb, TS, k, r.theta, r.dprev, alpha, r.st.beta_p * r.st.beta_p);
+        else th = ritz_top_cold(Ta, Tb, TS, k);
+        const bool have_prev = (r.kth == k - 1);
+        r.theta_prev = r.theta;
+        r.theta = th;
+        r.kth = k;
+        r.dprev = have_prev ? r.theta - r.theta_prev : 0.0;
+        if (k >= kc0 && have_prev && r.theta - r.theta_prev <= p.tol * r.theta) return 0;
     }
-    if (status != 5 && kth != ksteps && ksteps >= 1) {
-        theta = (ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, TS, ksteps);
-        kth = ksteps;
+    return k >= kmax ? 2 : -1;
+}
+
+// sigma = 2^(-e1) / sqrt(theta) from the final Ritz value (recomputed when the last
+// step's was skipped); UNDERFLOW (5, sigma = 0) when theta left the double range.
+template <int KL, int KU>
+__device__ __forceinline__ int lz_finish(double *const Ta, double *const Tb, LzRun &r, int status, double &sigma)
+{
+    constexpr int64_t TS = 32;
+    sigma = 0.0;
+    if (status != 5 && r.kth != r.ksteps && r.ksteps >= 1) {
+        r.theta = (r.ksteps == 1) ? Ta[0] : ritz_top_cold(Ta, Tb, TS, r.ksteps);
+        r.kth = r.ksteps;
     }
     if (status != 5) {
-        if (!(theta > 0.0) || !(theta <= 1.7e308)) {
-            status = 5;
-        } else {
-            sigma = (1.0 / sqrt(theta)) * pow2i(clampi(-st.e1, -1022, 1023));
-        }
+        if (!(r.theta > 0.0) || !(r.theta <= 1.7e308)) status = 5;
+        else sigma = (1.0 / sqrt(r.theta)) * pow2i(clampi(-r.st.e1, -1022, 1023));
     }
     if (status == 5) sigma = 0.0;
+    return status;
+}
+
+// Lanczos on H' for the point held by this lane, after band_lu: steps until the
+// stopping test, beta = 0 or k_max. Returns the point's status (0 OK, 2
+// NOT_CONVERGED, 5 UNDERFLOW) and sets sigma, the steps taken, the final Ritz value
+// theta (in H' units) and the Lanczos scalars st.
+template <int KL, int KU>
+__device__ __forceinline__ int lanczos_sigma(const KParams &p, const Mat &M, char *const rows, uint8_t *const pivs,
+                                             double *const Ta, double *const Tb, LzState &st, double &sigma, int &ksteps,
+                                             double &theta)
+{
+    LzRun r;
+    int status;
+    while ((status = lz_advance<KL, KU>(p, M, rows, pivs, Ta, Tb, r)) < 0) {
+    }
+    status = lz_finish<KL, KU>(Ta, Tb, r, status, sigma);
+    st = r.st;
+    ksteps = r.ksteps;
+    theta = r.theta;
     return status;
 }
 
@@ -706,6 +730,20 @@ __device__ __forceinline__ int64_t group_anchor(const KParams &p, const Mat &M, 
     const int ty = (int)(g / tiles_x), tx = (int)(g - (int64_t)ty * tiles_x);
     const int i = min(ty * 4 + 1, M.ny - 1), j = min(tx * 8 + 3, M.nx - 1);
     return (int64_t)i * M.nx + j;
+}
+
+// Outputs of one point: sigma, the eps-mask bits, status and steps.
+__device__ __forceinline__ void write_point(const KParams &p, int64_t flat, double sigma, int status, int ksteps)
+{
+    p.sigma[flat] = sigma;
+    if (p.mask) {
+        uint32_t bits = 0;
+        const unsigned long long sb = abs_bits(sigma);
+        for (int l = 0; l < p.n_eps; ++l) bits |= (sb <= abs_bits(p.eps[l]) ? 1u : 0u) << l;
+        p.mask[flat] = bits;
+    }
+    if (p.status) p.status[flat] = (int8_t)status;
+    if (p.steps) p.steps[flat] = ksteps;
 }
 
 template <int KL, int KU>
@@ -816,17 +854,7 @@ __global__ void __launch_bounds__(kThreads, Shape<KL, KU>::MIN_BLOCKS) k_sigma_m
                 atomicAdd(&p.sched_hist[b], 1);
                 continue;
             }
-            flat += M.out_off;
-            p.sigma[flat] = sigma;
-            if (p.mask) {
-                uint32_t bits = 0;
-                const unsigned long long sb = abs_bits(sigma);
-                for (int l = 0; l < p.n_eps; ++l)
-                    bits |= (sb <= abs_bits(p.eps[l]) ? 1u : 0u) << l;
-                p.mask[flat] = bits;
-            }
-            if (p.status) p.status[flat] = (int8_t)status;
-            if (p.steps) p.steps[flat] = ksteps;
+            write_point(p, flat + M.out_off, sigma, status, ksteps);
         }
     }
 #undef FLD
