@@ -225,3 +225,30 @@ def test_seed_changes_start_vector_not_result():
     z = oracle.grid_points(grid).ravel()
     bad, info = check_sigma(s1, s0, band_norm1(bands, kl, ku, z))
     assert not bad.any(), info
+
+
+def test_single_call_graph_capture_replays_bitwise():
+    """psa_sigma_min allocates nothing and copies nothing, so a call captured in a CUDA
+    graph replays to the same bits (and re-reads the bands at every replay)."""
+    bands, kl, ku, a = inputs.random_toeplitz(200, 2, 5, seed=5)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 33, 21)
+    b = torch.as_tensor(bands, device=DEV)
+    ws = psa.Workspace(200, kl, ku, 1024, device=DEV, npoints=grid.npoints)
+    ref = psa.sigma_min(b, kl, ku, grid, eps=(1e-2,), workspace=ws)
+    out = psa.sigma_min(b, kl, ku, grid, eps=(1e-2,), workspace=ws)  # outputs the graph writes
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        psa.sigma_min(b, kl, ku, grid, eps=(1e-2,), workspace=ws, out=out,
+                      stream=torch.cuda.current_stream())
+    out.sigma.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.sigma.cpu().numpy(), ref.sigma.cpu().numpy())
+    np.testing.assert_array_equal(out.mask.cpu().numpy(), ref.mask.cpu().numpy())
+    b.mul_(0.5)  # new band values: the replay reads them
+    g.replay()
+    ref2 = psa.sigma_min(b, kl, ku, grid, eps=(1e-2,))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.sigma.cpu().numpy(), ref2.sigma.cpu().numpy())
+    assert not np.array_equal(ref2.sigma.cpu().numpy(), ref.sigma.cpu().numpy())
