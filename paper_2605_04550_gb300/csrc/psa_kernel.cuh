@@ -42,7 +42,9 @@
 // consecutive entries of the list. A short estimate pass (one anchor point per
 // group, a few Lanczos steps) lets the groups be taken longest first, so the
 // launch does not end on a few slow groups. Each warp owns one contiguous
-// workspace block.
+// workspace block. In a batch launch (one band shape, many matrices) a group is a
+// tile of one of the matrices: the warp finds the matrix by a binary search in the
+// device plan, and its workspace block is sized for the largest matrix.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
