@@ -392,3 +392,37 @@ def test_gradient_formula_matches_finite_differences(case):
         fda = complex((sp - sm) / (2 * h), (spi - smi) / (2 * h))
         gb = oracle.dense_grad_to_bands(gA, kl, ku)
         assert abs(gb[d + kl, i] - fda) <= 1e-6 * abs(fda) + 1e-9, (gb[d + kl, i], fda)
+
+
+def _hard_points_n2000():
+    """Points of the n = 2000 Toeplitz grid (kl = 2, ku = 5, 512 x 512 over the symbol
+    box +20 %) where the stopping rule can fail: the 14 that need the most Lanczos
+    steps among 384 random grid points (outside the symbol curve, 40-300 steps), 4
+    on the edge of the curve (sigma / |zI - A|_1 in [1e-8, 1e-6), [1e-5, 1e-4),
+    [1e-4, 1e-3) and [1e-3, 1e-2)) and 2 inside (far below the roundoff floor)."""
+    bands, kl, ku, a = inputs.random_toeplitz(2000, 2, 5, seed=0)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 512, 512)
+    rng = np.random.default_rng(11)
+    z = oracle.grid_points(grid).ravel()[rng.choice(grid.npoints, 384, replace=False)]
+    s, st, k = oracle.sigma_min_banded(bands, kl, ku, z, k_max=1000, tol=1e-13)
+    rel = s / band_norm1(bands, kl, ku, z)
+    hard = np.argsort(-k, kind="stable")[:14]
+    edge = np.array([np.flatnonzero((rel >= lo) & (rel < 10 * lo) if lo != 1e-8 else (rel >= lo) & (rel < 1e-6))[0]
+                     for lo in (1e-8, 1e-5, 1e-4, 1e-3)])
+    inside = np.flatnonzero(rel < 1e-20)[:2]
+    return bands, kl, ku, z[np.concatenate([hard, edge, inside])], k[hard]
+
+
+def test_oracle_n2000_matches_dense_svd_where_lanczos_is_slow():
+    """The stopping rule at the benchmark's order: the oracle in both its exact tier
+    (tol 1e-15) and the library's settings (tol 1e-13, k_max 1000) against the dense
+    SVD (paper Sec. 2.1) at points that need tens to hundreds of Lanczos steps."""
+    bands, kl, ku, z, k_hard = _hard_points_n2000()
+    assert k_hard.min() >= 40, k_hard  # the points really are slow to converge
+    ref = oracle.sigma_min_dense(oracle.band_to_dense(bands, kl, ku), z)
+    nrm = band_norm1(bands, kl, ku, z)
+    for kw in ({}, {"k_max": 1000, "tol": 1e-13}):
+        s, st, _ = oracle.sigma_min_banded(bands, kl, ku, z, **kw)
+        bad, info = check_sigma(s, ref, nrm)
+        assert not bad.any(), (kw, info, s[bad], ref[bad])
+        assert info["max_rel_well"] <= 1e-10, (kw, info)
