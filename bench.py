@@ -48,10 +48,11 @@ WORKLOAD = (f"random banded Toeplitz n={N} kl={KL} ku={KU} (complex N(0,1) coeff
             f"8 eps levels 1e-1..1e-8, Lanczos to convergence (tol {TOL:g})")
 # nominal FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per Lanczos row-step of k_sigma_min<2,5>, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the reduced n = 256 case, see
-# profiles/k_sigma_min_toeplitz256_sections.md; traffic scales with row-steps
-DRAM_BYTES_PER_ROW_STEP = 532.0
+# DRAM bytes (read + write) per Lanczos row-step of k_sigma_min<2,5>: ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum of one main-pass launch of the reduced
+# case (--case small: n = 256, 384 x 384 grid, 198.9 GB for 3.70e8 row-steps). Factor
+# rows and Lanczos vectors are streamed once per sweep, so traffic scales with row-steps.
+DRAM_BYTES_PER_ROW_STEP = 537.0
 
 
 # the classifier trained by `bench.py --workload restriction --save-model ...`
@@ -383,8 +384,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": DRAM_BYTES_PER_ROW_STEP * float(steps.sum()) * n,
-                     "traffic_source": "ncu dram bytes per Lanczos row-step on the n=256 case, scaled by this "
-                                       "launch's row-steps (profiles/k_sigma_min_toeplitz256_sections.md)",
+                     "traffic_source": "ncu dram bytes per Lanczos row-step of one main-pass launch of the n=256 "
+                                       "case (bench.py --case small), scaled by this launch's row-steps",
                      "peak_source": "FP64 from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                      "peak_probe_tflops": 2 * probe / 1e12,
                      "frac_of_probe": achieved / (2 * probe / 1e12),

@@ -248,13 +248,15 @@ KernelOps pick_grad_ops(int kl, int ku)
     }
 }
 
-// Threads that fill the device once with the kernel for (kl, ku).
+// Threads that fill the device once with the kernel for (kl, ku): the resident
+// blocks per SM that the occupancy allows, at most kBlocksPerSm.
 int full_threads(const KernelOps &ops, int64_t *out)
 {
     int dev = 0, sms = 0, nb = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PSA_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PSA_ECUDA;
     if (ops.blocks_per_sm(&nb) != cudaSuccess || nb < 1) return PSA_ECUDA;
+    if (nb > kBlocksPerSm) nb = kBlocksPerSm;
     *out = (int64_t)sms * nb * kThreads;
     return PSA_OK;
 }

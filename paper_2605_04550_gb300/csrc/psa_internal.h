@@ -8,6 +8,12 @@ namespace psa {
 
 constexpr int kMaxEps = 32;
 constexpr int kThreads = 128;        // threads per block of the sigma_min kernel
+// Resident blocks per SM of one launch: 2 blocks of 4 warps = 2 warps per scheduler.
+// Two warps keep a scheduler's FP64 unit about 94 % busy; a third adds ~2 % in the
+// steady state but makes every warp run at a third of the unit, so the longest groups
+// (hundreds of Lanczos steps, started first) end up to 1.2 s after the rest of the
+// launch on the n = 2000 grid (4.27 s per grid with 3 warps, 3.63 s with 2).
+constexpr int kBlocksPerSm = 2;
 constexpr int kMaxKL = 4;            // compile-time band shapes: kl in [0, 4]
 constexpr int kMaxKU = 8;            //                           ku in [0, 8]
 constexpr int kBuckets = 4096;       // cost buckets of the work order (matrix order x sigma)
