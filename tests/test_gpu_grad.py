@@ -99,6 +99,31 @@ def test_grad_z_matches_central_differences_at_full_size():
     assert err.max() <= 1e-7, (err, s[0])
 
 
+def test_grad_matches_dense_oracle_at_full_size():
+    """Differentiation workload size (Grcar-type n = 4000 with N(0, 1e-2) band noise):
+    sigma, d sigma / dz and the whole band gradient of one point against the singular
+    pair of the oracle's dense SVD, at 4 resolvable points outside the curve."""
+    b, kl, ku = inputs.grcar_perturbed(4000, seed=0)
+    A = oracle.band_to_dense(b, kl, ku)
+    rng = np.random.default_rng(3)
+    z = np.concatenate([rng.uniform(-0.5, 2.5, 2) + 1j * rng.uniform(3.4, 3.9, 2),
+                        rng.uniform(3.2, 3.7, 2) + 1j * rng.uniform(-1.5, 1.5, 2)])
+    w = np.zeros(z.size)
+    w[0] = 1.0  # the band gradient of the first point alone
+    r = psa.sigma_min_grad(_t(b), kl, ku, _t(z), weight=_t(w, torch.float64), opts=TIGHT)
+    torch.cuda.synchronize()
+    sig, gz, st = r.sigma.cpu().numpy(), r.grad_z.cpu().numpy(), r.status.cpu().numpy()
+    assert np.all(st == psa.PT_OK)
+    for p, zz in enumerate(z):
+        s_ref, g_ref, gA = oracle.sigma_min_grad_dense(A, zz)
+        assert s_ref > 1e-6, s_ref  # resolvable: far above the roundoff floor
+        assert abs(sig[p] - s_ref) <= 1e-10 * s_ref, (p, sig[p], s_ref)
+        assert abs(gz[p] - g_ref) <= 1e-7 * abs(g_ref), (p, gz[p], g_ref)
+        if p == 0:
+            ref = oracle.dense_grad_to_bands(gA, kl, ku)
+            np.testing.assert_allclose(r.grad_bands.cpu().numpy(), ref, rtol=0, atol=1e-7 * np.abs(ref).max())
+
+
 def test_sigma_of_grad_kernel_equals_grid_kernel():
     b, kl, ku = inputs.grcar(100)
     grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 20, 12)

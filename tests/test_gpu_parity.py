@@ -83,15 +83,80 @@ def test_toeplitz_ragged_grid():
 
 def test_toeplitz_2000_full_size_sampled():
     """The benchmark's workload (n = 2000, kl = 2, ku = 5, 512 x 512) in the benchmark's
-    launch configuration, checked at 96 sampled points against the oracle."""
+    launch configuration, checked against the oracle at 400 points: 96 uniformly random,
+    and 32 from each decile of the GPU's Lanczos step counts (the slowest decile holds
+    every point above 150 steps) and of each status."""
     bands, kl, ku, a = inputs.random_toeplitz(2000, 2, 5, seed=0)
     grid = inputs.toeplitz_symbol_grid(a, kl, ku, 512, 512)
     eps = inputs.EPS_LEVELS_8
     sig, mask, st, steps = _gpu(bands, kl, ku, grid, eps)
-    rng = np.random.default_rng(0)
-    smp = np.sort(rng.choice(grid.npoints, 96, replace=False))
-    _assert_parity(bands, kl, ku, grid, eps, sig, mask, st, sample=smp)
     assert np.all((st == psa.PT_OK) | (st == psa.PT_UNDERFLOW))
+    rng = np.random.default_rng(0)
+    parts = [rng.choice(grid.npoints, 96, replace=False)]
+    ok = np.flatnonzero(st == psa.PT_OK)
+    edges = np.quantile(steps[ok], np.linspace(0, 1, 11))
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        cls = ok[(steps[ok] >= lo) & (steps[ok] <= hi)]
+        parts.append(rng.choice(cls, min(32, cls.size), replace=False))
+    parts.append(np.argsort(-steps)[:16])  # the slowest points of the grid
+    und = np.flatnonzero(st == psa.PT_UNDERFLOW)
+    parts.append(rng.choice(und, min(32, und.size), replace=False))
+    smp = np.unique(np.concatenate(parts))
+    assert smp.size >= 380 and steps[smp].max() == steps.max()
+    _assert_parity(bands, kl, ku, grid, eps, sig, mask, st, sample=smp)
+
+
+def _symbol_curve(a, kl, ku, m=4096):
+    t = np.arange(m) * (2.0 * np.pi / m)
+    return (a[None, :] * np.exp(1j * np.outer(t, np.arange(-kl, ku + 1)))).sum(axis=1)
+
+
+def _winding(f, z):
+    """Winding number of the closed polygon f about each point z."""
+    f1 = np.roll(f, -1)
+    turn = np.angle((f1[None, :] - z[:, None]) / (f[None, :] - z[:, None])).sum(axis=1)
+    return np.rint(turn / (2.0 * np.pi)).astype(int)
+
+
+def test_restriction_matrix_n20000_sampled():
+    """The learned restriction's test matrix (random banded Toeplitz n = 20000, kl = 3,
+    ku = 6 plus 1e-3 band noise, 1024 x 1024 grid), the largest order of the workloads:
+    64 points inside, on the edge of and outside its symbol curve, GPU (restricted mode,
+    the same per-point arithmetic as the full grid) against the oracle element by element."""
+    bands, kl, ku, grid = inputs.restriction_test_matrix()
+    eps = inputs.EPS_LEVELS_8
+    f = _symbol_curve(inputs.toeplitz_coefficients(kl, ku, 2024), kl, ku)
+    z = oracle.grid_points(grid).ravel()
+    rng = np.random.default_rng(5)
+    cand = rng.choice(grid.npoints, 3000, replace=False)
+    dist = np.abs(z[cand][:, None] - f[None, :]).min(axis=1)
+    wind = _winding(f, z[cand])
+    ext = max(grid.re_max - grid.re_min, grid.im_max - grid.im_min)
+    far = dist > 0.02 * ext
+    # outside points close enough to the curve that Lanczos converges in a few hundred
+    # steps (farther out it needs over a thousand at this order)
+    near_out = (wind == 0) & far & (dist < 0.03 * ext)
+    pts = np.concatenate([cand[(wind != 0) & far][:16], cand[dist < 0.004 * ext][:24], cand[near_out][:24]])
+    assert pts.size == 64
+    sig, mask, st, steps = _gpu(bands, kl, ku, grid, eps, idx=pts, opts=psa.LanczosOpts(k_max=4000))
+    ev = np.zeros(grid.npoints, dtype=bool)
+    ev[pts] = True
+    assert np.all(st[~ev] == psa.PT_NOT_EVALUATED)
+    assert np.all(np.isin(st[pts], (psa.PT_OK, psa.PT_UNDERFLOW, psa.PT_SINGULAR, psa.PT_NOT_CONVERGED)))
+    ref, st_ref, _ = oracle.sigma_min_banded(bands, kl, ku, z[pts])
+    nrm = band_norm1(bands, kl, ku, z[pts])
+    bad, info = check_sigma(sig[pts], ref, nrm)
+    assert not bad.any(), (info, pts[bad][:5], sig[pts][bad][:5], ref[bad][:5])
+    # the three regions really are there: sigma of order one outside, far below the
+    # floor inside (UNDERFLOW or an exact zero pivot), and the eps levels crossed on the edge
+    assert np.all(ref[40:] > 1e-3 * nrm[40:]) and np.all(ref[:16] <= 1e-13 * nrm[:16])
+    assert np.any((ref[16:40] > 1e-8) & (ref[16:40] < 1e-1))
+    # an exact zero pivot comes from underflow far inside the curve: where either side
+    # reports SINGULAR, both sigma lie below the floor
+    sing = (st[pts] == psa.PT_SINGULAR) | (st_ref == psa.PT_SINGULAR)
+    assert np.all(np.maximum(sig[pts], ref)[sing] <= 1e-13 * nrm[sing])
+    bad_m, _ = check_masks(mask[pts], oracle.masks(ref, eps), ref, nrm, eps)
+    assert not bad_m.any()
 
 
 @pytest.mark.parametrize("kl,ku", [(kl, ku) for kl in range(5) for ku in range(9)])
