@@ -264,6 +264,29 @@ int full_threads(const KernelOps &ops, int64_t *out)
 }  // namespace
 }  // namespace psa
 
+namespace psa {
+// The argument checks of psa_sigma_min (everything but the workspace), shared with
+// psa_sigma_min_static so that both report the same codes.
+int check_sigma_min_args(const psa_band *A, const psa_grid *g, const double *eps, int32_t n_eps,
+                         const int32_t *idx, int64_t n_idx, const double *sigma, const psa_lanczos_opts *opts)
+{
+    if (!band_ok(A) || !A->bands || !g || !sigma) return PSA_EINVAL;
+    if (!(std::isfinite(g->re_min) && std::isfinite(g->re_max) && std::isfinite(g->im_min) &&
+          std::isfinite(g->im_max)) ||
+        g->re_min > g->re_max || g->im_min > g->im_max || g->nx < 1 || g->ny < 1)
+        return PSA_EINVAL;
+    if ((int64_t)g->nx * g->ny > 2147483647LL) return PSA_EINVAL;
+    if (n_eps < 0 || n_eps > kMaxEps || (n_eps > 0 && !eps)) return PSA_EINVAL;
+    for (int l = 0; l < n_eps; ++l)
+        if (!std::isfinite(eps[l]) || !(eps[l] > 0.0)) return PSA_EINVAL;
+    if (n_idx < 0 || (n_idx > 0 && !idx)) return PSA_EINVAL;
+    if (!opts_ok(opts ? *opts : psa_default_opts())) return PSA_EINVAL;
+    if (A->kl > kMaxKL || A->ku > kMaxKU || !fits_row_offsets(A)) return PSA_EUNSUPPORTED;
+    if (!pick_ops(A->kl, A->ku).launch) return PSA_EUNSUPPORTED;
+    return PSA_OK;
+}
+}  // namespace psa
+
 using namespace psa;
 
 extern "C" {
@@ -322,22 +345,11 @@ int psa_sigma_min(const psa_band *A, const psa_grid *g, const double *eps, int32
                   int64_t n_idx, double *sigma, uint32_t *mask, int8_t *status, int32_t *steps,
                   const psa_lanczos_opts *opts, void *workspace, size_t ws_bytes, void *stream_ptr)
 {
-    if (!band_ok(A) || !A->bands || !g || !sigma) return PSA_EINVAL;
-    if (!(std::isfinite(g->re_min) && std::isfinite(g->re_max) && std::isfinite(g->im_min) &&
-          std::isfinite(g->im_max)) ||
-        g->re_min > g->re_max || g->im_min > g->im_max || g->nx < 1 || g->ny < 1)
-        return PSA_EINVAL;
+    const int arc = check_sigma_min_args(A, g, eps, n_eps, idx, n_idx, sigma, opts);
+    if (arc != PSA_OK) return arc;
     const int64_t ngrid = (int64_t)g->nx * g->ny;
-    if (ngrid > 2147483647LL) return PSA_EINVAL;
-    if (n_eps < 0 || n_eps > kMaxEps || (n_eps > 0 && !eps)) return PSA_EINVAL;
-    for (int l = 0; l < n_eps; ++l)
-        if (!std::isfinite(eps[l]) || !(eps[l] > 0.0)) return PSA_EINVAL;
-    if (n_idx < 0 || (n_idx > 0 && !idx)) return PSA_EINVAL;
     const psa_lanczos_opts o = opts ? *opts : psa_default_opts();
-    if (!opts_ok(o)) return PSA_EINVAL;
-    if (A->kl > kMaxKL || A->ku > kMaxKU || !fits_row_offsets(A)) return PSA_EUNSUPPORTED;
     const KernelOps ops = pick_ops(A->kl, A->ku);
-    if (!ops.launch) return PSA_EUNSUPPORTED;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PSA_EWORKSPACE;
 
     const int64_t npts = idx ? n_idx : ngrid;

@@ -109,6 +109,14 @@ struct KernelOps {
     cudaError_t (*blocks_per_sm)(int *);  // resident blocks of kThreads per SM
 };
 
+}  // namespace psa
+#include "psa.h"
+namespace psa {
+// Argument checks of psa_sigma_min other than the workspace (PSA_OK or the code that
+// psa_sigma_min would return); psa_abi.cu.
+int check_sigma_min_args(const psa_band *A, const psa_grid *g, const double *eps, int32_t n_eps,
+                         const int32_t *idx, int64_t n_idx, const double *sigma, const psa_lanczos_opts *opts);
+
 // One entry per compiled (kl, ku); defined in psa_inst_kl*.cu (sigma_min) and
 // psa_grad_kl*.cu (sigma_min with gradients).
 KernelOps kernel_ops_kl0(int ku);

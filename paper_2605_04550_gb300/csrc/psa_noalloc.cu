@@ -9,33 +9,25 @@
 // that the module carries for as long as the library is loaded.
 //
 // The host may not use the array's name as a device address (in host code it
-// names a host-side stand-in), so the device address is looked up with
-// cudaGetSymbolAddress, once per device with that device current, and cached.
+// names a host-side stand-in), so every call looks the device address up with
+// cudaGetSymbolAddress on the current device. The lookup allocates nothing, and
+// doing it per call keeps the address right when the device's context is torn
+// down and created again (cudaDeviceReset), which may load the module elsewhere.
 #include <cuda_runtime.h>
-#include <mutex>
 
 #include "psa.h"
+#include "psa_internal.h"
 
 namespace {
 
 __device__ __align__(256) unsigned char g_static_scratch[PSA_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up once).
+// Device address of g_static_scratch in the current device's context.
 int static_scratch(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSA_ECUDA;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return PSA_ECUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return PSA_ECUDA;
+    *out = p;
     return PSA_OK;
 }
 
@@ -45,7 +37,10 @@ extern "C" int psa_sigma_min_static(const psa_band *A, const psa_grid *g, const 
                                     const int32_t *idx, int64_t n_idx, double *sigma, uint32_t *mask,
                                     int8_t *status, int32_t *steps, const psa_lanczos_opts *opts, void *stream)
 {
-    // the problem must fit the fixed scratch with at least one warp (32 points) in flight
+    // the arguments first (the codes of psa_sigma_min), then the size: the problem
+    // must fit the fixed scratch with at least one warp (32 points) in flight
+    const int arc = psa::check_sigma_min_args(A, g, eps, n_eps, idx, n_idx, sigma, opts);
+    if (arc != PSA_OK) return arc;
     size_t need = 0;
     const int rc = psa_workspace_bytes(A, opts, 32, 0, &need);
     if (rc != PSA_OK) return rc;

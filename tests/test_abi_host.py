@@ -117,3 +117,29 @@ def _call(lib, *, n=10, kl=1, ku=1, bands=1 << 20, grid=(-1.0, 1.0, -1.0, 1.0, 4
 def test_sigma_min_rejects_bad_arguments(lib, kw, code):
     # every rejection happens on the host, before any device call
     assert _call(lib, **kw) == code
+
+
+def _call_static(lib, *, n=10, kl=1, ku=1, bands=1 << 20, grid=(-1.0, 1.0, -1.0, 1.0, 4, 4), eps=(0.1,),
+                 sigma=1 << 21, opts=None, null_grid=False):
+    A = _native.PsaBand(n, kl, ku, bands)
+    g = _native.PsaGrid(*grid)
+    e = (ctypes.c_double * max(len(eps), 1))(*eps)
+    o = opts if opts is not None else _native.PsaLanczosOpts(2, 1000, 1e-13, 0)
+    return lib.psa_sigma_min_static(ctypes.byref(A), None if null_grid else ctypes.byref(g), e, len(eps),
+                                    None, 0, sigma, None, None, None, ctypes.byref(o), None)
+
+
+@pytest.mark.parametrize("kw,code", [
+    # argument errors keep psa_sigma_min's codes even for problems beyond the static scratch
+    (dict(n=20000, kl=5, ku=6), _native.PSA_EUNSUPPORTED),
+    (dict(n=20000, kl=3, ku=9), _native.PSA_EUNSUPPORTED),
+    (dict(n=20000, kl=3, ku=6, null_grid=True), _native.PSA_EINVAL),
+    (dict(n=20000, kl=3, ku=6, eps=(0.0,)), _native.PSA_EINVAL),
+    (dict(n=20000, kl=3, ku=6, sigma=None), _native.PSA_EINVAL),
+    (dict(n=20000, kl=3, ku=6, bands=None), _native.PSA_EINVAL),
+    # a valid problem that needs more than the scratch (about 134 MB for one warp)
+    (dict(n=20000, kl=3, ku=6), _native.PSA_ESTATIC),
+])
+def test_static_entry_point_rejects_on_the_host(lib, kw, code):
+    # every rejection happens before any device call (no GPU here)
+    assert _call_static(lib, **kw) == code
