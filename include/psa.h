@@ -221,9 +221,11 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
  * loads the library holds until the process exits. It allocates nothing and
  * calls no allocating routine; outputs and inputs remain the caller's.
  *
- *  - Set-up: the first call on a device, with that device current, looks up
- *    the array's device address (cudaGetSymbolAddress) and caches it; make
- *    that first call before any stream capture.
+ *  - Set-up: every call looks up the array's device address on the current
+ *    device (cudaGetSymbolAddress, no allocation), so the address stays right
+ *    after cudaDeviceReset. The first call on a device may load the library's
+ *    device code into its context; make that first call before any stream
+ *    capture.
  *  - Size limit: the scratch must hold at least one warp of points (see
  *    psa_workspace_bytes with points_in_flight = 32); larger problems are
  *    rejected with PSA_ESTATIC and nothing is launched. Within the limit the
@@ -233,8 +235,10 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
  *    call's contents (each call clears the parts that must start at zero).
  *    Calls whose kernels may overlap on the GPU (different streams, or
  *    several host threads) race on the array: serialise them.
- * Results are those of psa_sigma_min on the same arguments.
- * Errors: as psa_sigma_min, plus PSA_ESTATIC. */
+ * Results are bitwise those of psa_sigma_min on the same arguments (a point's
+ * arithmetic does not depend on how many points are in flight).
+ * Errors: the argument codes of psa_sigma_min (PSA_EINVAL, PSA_EUNSUPPORTED)
+ * first, then PSA_ESTATIC, then PSA_ECUDA. */
 int psa_sigma_min_static(const psa_band *A, const psa_grid *g,
                          const double *eps, int32_t n_eps,
                          const int32_t *idx, int64_t n_idx,
@@ -356,6 +360,17 @@ int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const dou
  * Errors: PSA_EINVAL, PSA_ECUDA. */
 int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
                   float *C, int64_t ldc, void *stream);
+
+/* Number of GEMM tiles (of psa_gemm_bf16, psa_mlp_forward and
+ * psa_mlp_train_step on the current device) whose bounded waits for a tensor-
+ * memory copy or a tensor-core commit ran out since the previous call, then
+ * reset to zero. A tile that times out writes NaN in place of its outputs (the
+ * outputs of that call are undefined), waits once more for the work it issued,
+ * frees its tensor memory and exits; the asynchronous calls themselves still
+ * return PSA_OK. SYNCHRONISES the device (it reads a device counter); call it
+ * where a result is read back anyway. The paper has no counterpart.
+ * Errors: PSA_EINVAL (count NULL), PSA_ECUDA. */
+int psa_mlp_timeouts(uint32_t *count);
 
 /* Bytes of device workspace for psa_mlp_forward over `rows` rows (training = 0;
  * rows beyond 131072 are processed in passes of 131072) or for

@@ -36,6 +36,7 @@ EXPORTS = (
     "psa_mlp_workspace_bytes",
     "psa_mlp_forward",
     "psa_mlp_train_step",
+    "psa_mlp_timeouts",
     "psa_matrix_stats",
     "psa_global_features",
     "psa_point_features",
@@ -138,6 +139,8 @@ def load(path: str | None = None):
         lib.psa_mlp_forward.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
         lib.psa_mlp_train_step.restype = ctypes.c_int
         lib.psa_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        lib.psa_mlp_timeouts.restype = ctypes.c_int
+        lib.psa_mlp_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
         lib.psa_matrix_stats.restype = ctypes.c_int
         lib.psa_matrix_stats.argtypes = [ctypes.POINTER(PsaBand), vp, vp, vp]
         lib.psa_global_features.restype = ctypes.c_int

@@ -73,6 +73,10 @@ struct GemmArgs {
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 
+// CTAs of k_gemm_bf16 whose bounded waits ran out since the last psa_mlp_timeouts
+// call (their outputs are NaN; the host learns of them through that call).
+__device__ unsigned int g_gemm_timeouts;
+
 __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
 {
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
         }
         ok = __syncthreads_and((done && ok) ? 1 : 0) != 0;
     }
+    if (!ok && tid == 0) atomicAdd(&g_gemm_timeouts, 1u);
     tc::fence_after_sync();
 
     // epilogue: thread = row m0 + 32 warp + lane, 32 columns per tensor-memory load
@@ -450,6 +455,17 @@ int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb
     g.C = C;
     g.ldc = ldc;
     return gemm(g, static_cast<cudaStream_t>(stream)) == cudaSuccess ? PSA_OK : PSA_ECUDA;
+}
+
+int psa_mlp_timeouts(uint32_t *count)
+{
+    if (!count) return PSA_EINVAL;
+    unsigned int v = 0;
+    const unsigned int zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_gemm_timeouts, sizeof(v)) != cudaSuccess) return PSA_ECUDA;
+    if (v && cudaMemcpyToSymbol(g_gemm_timeouts, &zero, sizeof(zero)) != cudaSuccess) return PSA_ECUDA;
+    *count = v;
+    return PSA_OK;
 }
 
 int psa_mlp_workspace_bytes(int64_t rows, int32_t training, size_t *bytes)

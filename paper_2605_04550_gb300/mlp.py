@@ -58,6 +58,16 @@ def gemm_bf16(A, B, stream=None):
     return C
 
 
+def check_timeouts() -> None:
+    """Raise if a tensor-core GEMM tile gave up on a bounded wait since the last check
+    (its outputs were written as NaN). Synchronises the device."""
+    lib = _native.load()
+    n = ctypes.c_uint32()
+    _native.check(lib.psa_mlp_timeouts(ctypes.byref(n)), "psa_mlp_timeouts")
+    if n.value:
+        raise _native.PsaError(_native.PSA_ECUDA, f"{n.value} GEMM tile(s) timed out waiting for the tensor cores")
+
+
 def workspace_bytes(rows: int, training: bool) -> int:
     lib = _native.load()
     out = ctypes.c_size_t()

@@ -276,6 +276,7 @@ class Restriction:
                 sel = order[b * batch:(b + 1) * batch]
                 tr.step(xt.index_select(0, sel), yt.index_select(0, sel))
             p = mlp.forward(self.theta, xv).cpu().numpy().astype(np.float64)
+            mlp.check_timeouts()  # the epoch's GEMMs all completed their waits
             p = np.clip(p, 1e-7, 1 - 1e-7)
             vloss = float(-np.mean(yv_np * np.log(p) + (1 - yv_np) * np.log(1 - p)))
             self.history.append({"epoch": ep, "val_loss": vloss, "seconds": time.perf_counter() - t0,

@@ -119,3 +119,13 @@ def test_training_learns_a_disk():
     torch.cuda.synchronize()
     acc = ((p > 0.5).float() == y).float().mean().item()
     assert acc >= 0.97, acc
+
+
+def test_no_gemm_tile_timed_out():
+    # every GEMM of this module's tests completed its bounded waits, and the counter
+    # reads back as zero after a check
+    A = torch.randn(300, 128, device=DEV).to(torch.bfloat16)
+    B = torch.randn(256, 128, device=DEV).to(torch.bfloat16)
+    mlp.gemm_bf16(A, B)
+    mlp.check_timeouts()
+    mlp.check_timeouts()
