@@ -361,8 +361,34 @@ int psa_sigma_min_batched(const void *plan_host, const void *plan_dev, const dou
 int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
                   float *C, int64_t ldc, void *stream);
 
-/* Number of GEMM tiles (of psa_gemm_bf16, psa_mlp_forward and
- * psa_mlp_train_step on the current device) whose bounded waits for a tensor-
+/* The paper's dual-path network (Sec. 3.2.2) on the same feature rows: a
+ * coordinate pathway on the Fourier columns [0, 26) (26 -> 64 -> 64, Eq. for
+ * h_c^(1), h_c^(2)), a matrix pathway on the feature columns [26, 60) (34 ->
+ * 128 -> 64; the paper has 33 features, this library's set is listed at
+ * psa_point_features), concatenation (128), the residual block h4 =
+ * SiLU(W4 h3 + b4), h5 = SiLU(W5 h4 + b5), h6 = h4 + h5 (128), h7 =
+ * SiLU(W7 h6 + b7) (64) and p = sigmoid(w . h7 + b). theta (DEVICE float32
+ * [PSA_DUAL_PARAMS]) stores fused, padded matrices [out][in], row-major:
+ *   WA[256][128], bA[256]: rows 0..63 = (W_c1, b_c1) on columns 0..25, rows
+ *     64..191 = (W_m1, b_m1) on columns 26..59, all else zero;
+ *   WB[128][256], bB[128]: rows 0..63 = W_c2 on columns 0..63, rows 64..127 =
+ *     W_m2 on columns 64..191 (so WB's output is [h_c2 | h_m2] = h3);
+ *   W4[128][128], b4, W5[128][128], b5;
+ *   W7[128][128], b7[128]: rows 0..63 = (W7, b7), rows 64..127 zero;
+ *   w[128] (entries 64..127 zero), b.
+ * The zero entries are structural: training masks their gradients, so they
+ * stay zero and the network has PSA_DUAL_TRAINABLE parameters. Same calling
+ * conventions, batching, asynchrony and errors as psa_mlp_*. */
+#define PSA_DUAL_PARAMS 115585
+#define PSA_DUAL_TRAINABLE 59969
+int psa_dual_workspace_bytes(int64_t rows, int32_t training, size_t *bytes);
+int psa_dual_forward(const float *theta, const uint16_t *x, int64_t rows, float *prob, void *workspace,
+                     size_t ws_bytes, void *stream);
+int psa_dual_train_step(float *theta, float *adam_m, float *adam_v, int32_t step, float lr, const uint16_t *x,
+                        const float *y, int64_t rows, float *loss, void *workspace, size_t ws_bytes, void *stream);
+
+/* Number of GEMM tiles (of psa_gemm_bf16, psa_mlp_* and psa_dual_* on the
+ * current device) whose bounded waits for a tensor-
  * memory copy or a tensor-core commit ran out since the previous call, then
  * reset to zero. A tile that times out writes NaN in place of its outputs (the
  * outputs of that call are undefined), waits once more for the work it issued,

@@ -37,6 +37,9 @@ EXPORTS = (
     "psa_mlp_forward",
     "psa_mlp_train_step",
     "psa_mlp_timeouts",
+    "psa_dual_workspace_bytes",
+    "psa_dual_forward",
+    "psa_dual_train_step",
     "psa_matrix_stats",
     "psa_global_features",
     "psa_point_features",
@@ -48,6 +51,7 @@ EXPORTS = (
 SYMBOL_SAMPLES, STATS, GLOBAL_FEATURES = 256, 24, 28
 
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 128, 256, 164865
+DUAL_PARAMS, DUAL_TRAINABLE = 115585, 59969
 
 BATCH_ORDER_AUTO, BATCH_ORDER_PLAN, BATCH_ORDER_ESTIMATE = 0, 1, 2
 
@@ -139,6 +143,12 @@ def load(path: str | None = None):
         lib.psa_mlp_forward.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
         lib.psa_mlp_train_step.restype = ctypes.c_int
         lib.psa_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        lib.psa_dual_workspace_bytes.restype = ctypes.c_int
+        lib.psa_dual_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psa_dual_forward.restype = ctypes.c_int
+        lib.psa_dual_forward.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        lib.psa_dual_train_step.restype = ctypes.c_int
+        lib.psa_dual_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
         lib.psa_mlp_timeouts.restype = ctypes.c_int
         lib.psa_mlp_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
         lib.psa_matrix_stats.restype = ctypes.c_int

@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "psa.h"
+#include "psa_gemm.h"
 #include "psa_tc.cuh"
 
 namespace psa {
@@ -45,8 +46,6 @@ constexpr int64_t OFF_B4 = OFF_W4 + HID;
 constexpr int64_t NPARAM = OFF_B4 + 1;
 static_assert(NPARAM == PSA_MLP_PARAMS, "parameter count");
 
-constexpr int TILE = 128;       // M and N of a CTA tile
-constexpr int KCH = 64;         // K per shared-memory chunk (4 MMAs of K = 16)
 constexpr int TILE_BYTES = TILE * KCH * 2;
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B tiles of one K chunk
 constexpr int STAGES = 3;
@@ -55,21 +54,6 @@ constexpr int STAGES = 3;
 constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 2048;
 constexpr int WAIT_LIMIT = 1 << 20;
 constexpr int64_t FWD_CHUNK = 131072;  // rows per forward pass through the workspace
-
-struct GemmArgs {
-    const __nv_bfloat16 *A;
-    int64_t lda;
-    const __nv_bfloat16 *B;
-    int64_t ldb;
-    int M, N, K;
-    const float *bias;  // [N] or null
-    float *C;           // FP32 (acc + bias), row-major, ldc; or null
-    int64_t ldc;
-    __nv_bfloat16 *H;   // BF16 silu(acc + bias), row-major, ldh; or null
-    int64_t ldh;
-    __nv_bfloat16 *Ht;  // BF16 silu(acc + bias), transposed ([N][M]), ldht; or null
-    int64_t ldht;
-};
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 
@@ -170,9 +154,12 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
             const int col = n0 + c0 + j;
             float z = ok ? __uint_as_float(r[j]) : qnan;  // a timed-out wait leaves NaN
             if (g.bias) z += g.bias[col];
+            if (g.Cadd) z += g.Cadd[(int64_t)row * g.ldcadd + col];
             if (g.C) g.C[(int64_t)row * g.ldc + col] = z;
             if (g.H || g.Ht) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(silu(z));
+                float a = silu(z);
+                if (g.R) a += __bfloat162float(g.R[(int64_t)row * g.ldr + col]);
+                const __nv_bfloat16 h = __float2bfloat16_rn(a);
                 if (g.H) g.H[(int64_t)row * g.ldh + col] = h;
                 if (g.Ht) g.Ht[(int64_t)col * g.ldht + row] = h;
             }

@@ -188,8 +188,9 @@ def _grow(flag):
 class Restriction:
     """The trained classifier with its calibrated thresholds."""
 
-    def __init__(self, device="cuda", seed: int = 0, eps: float = EPS):
-        self.theta = mlp.init_theta(seed, device)
+    def __init__(self, device="cuda", seed: int = 0, eps: float = EPS, net: str = "mlp"):
+        self.net = net
+        self.theta = mlp.init_theta(seed, device, net)
         self.device = device
         self.eps = eps
         self.tau = 0.5
@@ -201,7 +202,7 @@ class Restriction:
         """Parameters, threshold and calibration summary to an .npz file."""
         import json
         th = self.theta.detach().cpu().numpy().astype(np.float32)
-        info = {"tau": self.tau, "eps": self.eps, "meta": meta or {},
+        info = {"tau": self.tau, "eps": self.eps, "net": self.net, "meta": meta or {},
                 "calibration": {k: v for k, v in self.calibration.items() if k != "table"}}
         np.savez(path, theta=th, info=np.frombuffer(json.dumps(info).encode(), dtype=np.uint8))
 
@@ -211,10 +212,11 @@ class Restriction:
         import torch
         d = np.load(path)
         th = d["theta"]
-        if th.shape != (mlp.NPARAM,) or th.dtype != np.float32:
-            raise ValueError("parameter vector of the wrong size")
         info = json.loads(bytes(d["info"]).decode())
-        r = cls(device, eps=float(info["eps"]))
+        net = info.get("net", "mlp")
+        if th.shape != (mlp.nparam(net),) or th.dtype != np.float32:
+            raise ValueError("parameter vector of the wrong size")
+        r = cls(device, eps=float(info["eps"]), net=net)
         r.theta = torch.as_tensor(th, device=device)
         r.tau = float(info["tau"])
         r.calibration = info.get("calibration", {})
@@ -265,7 +267,7 @@ class Restriction:
         nv = max(int(S * holdout), 1)
         xv, yv = x.index_select(0, perm[:nv]), y.index_select(0, perm[:nv])
         xt, yt = x.index_select(0, perm[nv:]), y.index_select(0, perm[nv:])
-        tr = mlp.Trainer(self.theta, batch=batch, lr=lr)
+        tr = mlp.Trainer(self.theta, batch=batch, lr=lr, net=self.net)
         best, best_theta, bad = float("inf"), self.theta.clone(), 0
         yv_np = yv.cpu().numpy()
         for ep in range(epochs):
@@ -275,7 +277,7 @@ class Restriction:
             for b in range(nb):
                 sel = order[b * batch:(b + 1) * batch]
                 tr.step(xt.index_select(0, sel), yt.index_select(0, sel))
-            p = mlp.forward(self.theta, xv).cpu().numpy().astype(np.float64)
+            p = mlp.forward(self.theta, xv, net=self.net).cpu().numpy().astype(np.float64)
             mlp.check_timeouts()  # the epoch's GEMMs all completed their waits
             p = np.clip(p, 1e-7, 1 - 1e-7)
             vloss = float(-np.mean(yv_np * np.log(p) + (1 - yv_np) * np.log(1 - p)))
@@ -303,11 +305,11 @@ class Restriction:
         dev = ctx.bands.device
         nx, ny = grid.nx, grid.ny
         if not hierarchical:
-            return mlp.forward(self.theta, point_features(ctx, grid)).view(ny, nx)
+            return mlp.forward(self.theta, point_features(ctx, grid), net=self.net).view(ny, nx)
         ic = torch.arange(0, ny, 4, device=dev, dtype=torch.int32)
         jc = torch.arange(0, nx, 4, device=dev, dtype=torch.int32)
         cidx = (ic[:, None] * nx + jc[None, :]).reshape(-1).contiguous()
-        pc = mlp.forward(self.theta, point_features(ctx, grid, cidx))
+        pc = mlp.forward(self.theta, point_features(ctx, grid, cidx), net=self.net)
         t = self.tau if tau is None else tau
         tc = min(float(torch.quantile(pc.float(), 0.8).item()), t)
         flag = _grow((pc >= tc).view(ic.numel(), jc.numel()))
@@ -321,7 +323,7 @@ class Restriction:
         fidx = (ii * nx + jj)[ok].to(torch.int32).contiguous()
         prob = torch.zeros(ny * nx, dtype=torch.float32, device=dev)
         if fidx.numel():
-            prob[fidx.long()] = mlp.forward(self.theta, point_features(ctx, grid, fidx))
+            prob[fidx.long()] = mlp.forward(self.theta, point_features(ctx, grid, fidx), net=self.net)
         self.last_counts = {"coarse": int(cidx.numel()), "fine": int(fidx.numel()), "tau_coarse": tc}
         return prob.view(ny, nx)
 
