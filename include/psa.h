@@ -363,14 +363,14 @@ int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb
 
 /* The paper's dual-path network (Sec. 3.2.2) on the same feature rows: a
  * coordinate pathway on the Fourier columns [0, 26) (26 -> 64 -> 64, Eq. for
- * h_c^(1), h_c^(2)), a matrix pathway on the feature columns [26, 60) (34 ->
+ * h_c^(1), h_c^(2)), a matrix pathway on the feature columns [26, 61) (35 ->
  * 128 -> 64; the paper has 33 features, this library's set is listed at
  * psa_point_features), concatenation (128), the residual block h4 =
  * SiLU(W4 h3 + b4), h5 = SiLU(W5 h4 + b5), h6 = h4 + h5 (128), h7 =
  * SiLU(W7 h6 + b7) (64) and p = sigmoid(w . h7 + b). theta (DEVICE float32
  * [PSA_DUAL_PARAMS]) stores fused, padded matrices [out][in], row-major:
  *   WA[256][128], bA[256]: rows 0..63 = (W_c1, b_c1) on columns 0..25, rows
- *     64..191 = (W_m1, b_m1) on columns 26..59, all else zero;
+ *     64..191 = (W_m1, b_m1) on columns 26..60, all else zero;
  *   WB[128][256], bB[128]: rows 0..63 = W_c2 on columns 0..63, rows 64..127 =
  *     W_m2 on columns 64..191 (so WB's output is [h_c2 | h_m2] = h3);
  *   W4[128][128], b4, W5[128][128], b5;
@@ -380,7 +380,7 @@ int psa_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb
  * stay zero and the network has PSA_DUAL_TRAINABLE parameters. Same calling
  * conventions, batching, asynchrony and errors as psa_mlp_*. */
 #define PSA_DUAL_PARAMS 115585
-#define PSA_DUAL_TRAINABLE 59969
+#define PSA_DUAL_TRAINABLE 60097
 int psa_dual_workspace_bytes(int64_t rows, int32_t training, size_t *bytes);
 int psa_dual_forward(const float *theta, const uint16_t *x, int64_t rows, float *prob, void *workspace,
                      size_t ws_bytes, void *stream);
@@ -473,10 +473,12 @@ int psa_global_features(const double *stats, const double *sigma4, double eps, f
  * the flat grid indices idx[0 .. n_idx) (DEVICE), written to x (DEVICE,
  * 16-byte aligned) in point order: [0, 26) the Fourier encoding [c, sin 2^k c,
  * cos 2^k c], k = 1..6, of the grid coordinates c scaled to [-1, 1]^2;
- * 26..28 the distances g1 (to the nearest symbol sample), g2 (to the
- * centroid), g3 (mean distance to the samples), in units of the symbol radius;
- * 29, 30 log10 of g1 and g3; 31 the winding number of the symbol curve about
- * the point; [32, 32 + PSA_GLOBAL_FEATURES) the global features; zeros after.
+ * 26..28 the distances g1 (to the closed polyline through the symbol samples),
+ * g2 (to the centroid), g3 (mean distance to the samples), in units of the
+ * symbol radius; 29, 30 log10 of g1 and g3; 31 the winding number of the
+ * symbol curve about the point; [32, 32 + PSA_GLOBAL_FEATURES) the global
+ * features; 32 + PSA_GLOBAL_FEATURES: log10 of the distance to the polyline
+ * over eps; zeros after.
  * Errors: PSA_EINVAL, PSA_ECUDA. */
 int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
                        const psa_c64 *symbol, const float *global, uint16_t *x, void *stream);

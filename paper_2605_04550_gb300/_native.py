@@ -51,7 +51,7 @@ EXPORTS = (
 SYMBOL_SAMPLES, STATS, GLOBAL_FEATURES = 256, 24, 28
 
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 128, 256, 164865
-DUAL_PARAMS, DUAL_TRAINABLE = 115585, 59969
+DUAL_PARAMS, DUAL_TRAINABLE = 115585, 60097
 
 BATCH_ORDER_AUTO, BATCH_ORDER_PLAN, BATCH_ORDER_ESTIMATE = 0, 1, 2
 

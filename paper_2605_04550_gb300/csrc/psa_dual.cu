@@ -32,7 +32,7 @@ using mlp::TILE;
 
 constexpr int IN = PSA_MLP_IN;        // feature row width (psa_point_features)
 constexpr int NC = 26;                // Fourier columns [0, 26)
-constexpr int MC0 = 26, NMF = 34;     // matrix-path columns [26, 60)
+constexpr int MC0 = 26, NMF = 35;     // matrix-path columns [26, 61)
 constexpr int HC = 64, HM1 = 128, HM2 = 64, H3 = 128, H7 = 64;
 constexpr int NA = 256;               // layer A outputs: [0, 64) coordinate, [64, 192) matrix, pad
 constexpr int NB = 128, NH = 128;     // layer B outputs (= h3) and the residual block's width

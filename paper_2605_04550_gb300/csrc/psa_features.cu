@@ -26,6 +26,7 @@ namespace psa {
 namespace feat {
 
 constexpr int T = PSA_SYMBOL_SAMPLES;
+constexpr int kPointFeatures = 33 + PSA_GLOBAL_FEATURES;  // nonzero columns of a feature row
 constexpr int NT = 1024;
 
 __device__ __forceinline__ double block_sum(double v, double *red)
@@ -268,15 +269,22 @@ __global__ void k_point_features(double re_min, double im_min, double hx, double
             v[2 + 4 * (k - 1) + 2] = cxx;
             v[2 + 4 * (k - 1) + 3] = cyy;
         }
-        // distances (about the centroid, in units of the curve's radius R) and winding
+        // distances (about the centroid, in units of the curve's radius R) and winding;
+        // dmin is the distance to the closed polyline through the samples (exact for a
+        // curve made of straight pieces, such as the segment of a kl = ku Grcar-type band,
+        // whose sensitive zone is a band of width about 2 eps around it)
         const float pr = (float)(zr - cr), pi = (float)(zi - ci);
         float dmin = INFINITY, dsum = 0.f, wind = 0.f;
         float2 prev = make_float2(sym[T - 1].x - pr, sym[T - 1].y - pi);
         for (int k = 0; k < T; ++k) {
             const float2 cur = make_float2(sym[k].x - pr, sym[k].y - pi);
-            const float d = sqrtf(cur.x * cur.x + cur.y * cur.y);
-            dmin = fminf(dmin, d);
-            dsum += d;
+            dsum += sqrtf(cur.x * cur.x + cur.y * cur.y);
+            // nearest point of the piece prev -> cur to the point (the origin here)
+            const float ex = cur.x - prev.x, ey = cur.y - prev.y;
+            const float ee = ex * ex + ey * ey;
+            const float t = ee > 0.f ? fminf(fmaxf(-(prev.x * ex + prev.y * ey) / ee, 0.f), 1.f) : 0.f;
+            const float qx = prev.x + t * ex, qy = prev.y + t * ey;
+            dmin = fminf(dmin, sqrtf(qx * qx + qy * qy));
             // angle swept from prev to cur about the point
             wind += atan2f(prev.x * cur.y - prev.y * cur.x, prev.x * cur.x + prev.y * cur.y);
             prev = cur;
@@ -289,9 +297,11 @@ __global__ void k_point_features(double re_min, double im_min, double hx, double
         v[30] = log10f(g3 + 1e-7f);
         v[31] = rintf(wind / 6.28318530718f);
         for (int k = 0; k < PSA_GLOBAL_FEATURES; ++k) v[32 + k] = gf[k];
+        // the distance to the curve against the level: log10(dmin / eps) (gf[24] = log10(eps / R))
+        v[32 + PSA_GLOBAL_FEATURES] = v[29] - gf[24];
         __nv_bfloat16 *row = x + p * PSA_MLP_IN;
-        for (int k = 0; k < 32 + PSA_GLOBAL_FEATURES; ++k) row[k] = __float2bfloat16_rn(v[k]);
-        for (int k = 32 + PSA_GLOBAL_FEATURES; k < PSA_MLP_IN; ++k) row[k] = __float2bfloat16_rn(0.f);
+        for (int k = 0; k < kPointFeatures; ++k) row[k] = __float2bfloat16_rn(v[k]);
+        for (int k = kPointFeatures; k < PSA_MLP_IN; ++k) row[k] = __float2bfloat16_rn(0.f);
     }
 }
 

@@ -4,7 +4,7 @@ through the C ABI).
 ``net="mlp"``: a multilayer perceptron IN -> 256 -> 256 -> 256 -> 1 with SiLU hidden
 units and a sigmoid output. ``net="dual"``: the paper's dual-path network (Sec.
 3.2.2): a coordinate pathway on the Fourier encoding (26 -> 64 -> 64), a matrix
-pathway on the other features (34 -> 128 -> 64), concatenation, a residual block
+pathway on the other features (35 -> 128 -> 64), concatenation, a residual block
 (128, h6 = h4 + h5), a 64-unit projection and a sigmoid output. Dense layers run as
 BF16 GEMMs on the tensor cores (FP32 accumulation); training is Adam on binary
 cross-entropy (paper Sec. 3.4). All parameters live in one float32 device vector
@@ -44,7 +44,7 @@ for _name, _r, _c in (("WA", 256, IN), ("bA", 256, 1), ("WB", 128, 256), ("bB", 
 assert _o == DUAL_NPARAM
 #: (block, row slice, column slice, fan_in) of every trainable weight block
 DUAL_WEIGHTS = (("WA", slice(0, 64), slice(0, 26), 26),       # W_c1: Fourier columns -> h_c1
-                ("WA", slice(64, 192), slice(26, 60), 34),    # W_m1: feature columns -> h_m1
+                ("WA", slice(64, 192), slice(26, 61), 35),    # W_m1: feature columns -> h_m1
                 ("WB", slice(0, 64), slice(0, 64), 64),       # W_c2
                 ("WB", slice(64, 128), slice(64, 192), 128),  # W_m2
                 ("W4", slice(0, 128), slice(0, 128), 128),

@@ -176,6 +176,25 @@ def recall_metrics(truth: np.ndarray, pred_region: np.ndarray) -> dict:
             "sensitive_fraction": float(t.mean())}
 
 
+#: column of a feature row holding log10(distance to the symbol polyline / eps)
+NEAR_COL = 32 + _native.GLOBAL_FEATURES
+#: points within NEAR_FACTOR * eps of the symbol curve always enter the region
+NEAR_FACTOR = 2.0
+
+
+def near_curve(x, grid: Grid, eps: float, coarse: bool = False):
+    """Boolean (rows,) from feature rows x: the point lies within NEAR_FACTOR * eps of the
+    symbol curve (for a coarse anchor of the hierarchical pass: within that band plus
+    the reach of its 4 x 4 cell). For banded Toeplitz-like A the curve itself lies in
+    Lambda_eps once n is large (sigma_min(zI - A) -> 0 on it), and sigma_min is
+    1-Lipschitz in z, so these points are sensitive or next to the zone; the rule
+    catches the thin zone of nearly normal matrices (a kl = ku Grcar-type band), which
+    is a band of width 2 eps about the spectrum that coarse training labels rarely hit."""
+    h = max((grid.re_max - grid.re_min) / max(grid.nx - 1, 1), (grid.im_max - grid.im_min) / max(grid.ny - 1, 1))
+    reach = NEAR_FACTOR * eps + (4.25 * h if coarse else 0.0)
+    return x[:, NEAR_COL].float() <= float(np.log10(reach / eps))
+
+
 def _grow(flag):
     """Flagged coarse cells plus their 8 neighbours: a cell whose own anchor falls just
     outside the zone still gets its fine points evaluated when a neighbouring anchor
@@ -305,14 +324,17 @@ class Restriction:
         dev = ctx.bands.device
         nx, ny = grid.nx, grid.ny
         if not hierarchical:
-            return mlp.forward(self.theta, point_features(ctx, grid), net=self.net).view(ny, nx)
+            x = point_features(ctx, grid)
+            p = mlp.forward(self.theta, x, net=self.net)
+            return torch.where(near_curve(x, grid, self.eps), torch.ones_like(p), p).view(ny, nx)
         ic = torch.arange(0, ny, 4, device=dev, dtype=torch.int32)
         jc = torch.arange(0, nx, 4, device=dev, dtype=torch.int32)
         cidx = (ic[:, None] * nx + jc[None, :]).reshape(-1).contiguous()
-        pc = mlp.forward(self.theta, point_features(ctx, grid, cidx), net=self.net)
+        xc = point_features(ctx, grid, cidx)
+        pc = mlp.forward(self.theta, xc, net=self.net)
         t = self.tau if tau is None else tau
         tc = min(float(torch.quantile(pc.float(), 0.8).item()), t)
-        flag = _grow((pc >= tc).view(ic.numel(), jc.numel()))
+        flag = _grow(((pc >= tc) | near_curve(xc, grid, self.eps, coarse=True)).view(ic.numel(), jc.numel()))
         # fine points of flagged cells
         fi = (ic[:, None] + torch.arange(4, device=dev, dtype=torch.int32)[None, :])  # (nyc, 4)
         fj = (jc[:, None] + torch.arange(4, device=dev, dtype=torch.int32)[None, :])  # (nxc, 4)
@@ -323,22 +345,38 @@ class Restriction:
         fidx = (ii * nx + jj)[ok].to(torch.int32).contiguous()
         prob = torch.zeros(ny * nx, dtype=torch.float32, device=dev)
         if fidx.numel():
-            prob[fidx.long()] = mlp.forward(self.theta, point_features(ctx, grid, fidx), net=self.net)
+            xf = point_features(ctx, grid, fidx)
+            pf = mlp.forward(self.theta, xf, net=self.net)
+            prob[fidx.long()] = torch.where(near_curve(xf, grid, self.eps), torch.ones_like(pf), pf)
         self.last_counts = {"coarse": int(cidx.numel()), "fine": int(fidx.numel()), "tau_coarse": tc}
         return prob.view(ny, nx)
 
     # ---------------------------------------------------------- calibration
     @staticmethod
-    def hierarchical_mask(full, tau: float):
+    def hierarchical_mask(full, tau: float, near_coarse=None):
         """The hierarchical map from the full fine map (the network gives every point
         the same value alone or in any batch): coarse points are full[::4, ::4];
         fine values survive in the 4 x 4 cells whose coarse value reaches
-        min(80th percentile, tau), zero elsewhere."""
+        min(80th percentile, tau) or whose anchor is near the curve (near_coarse),
+        and their neighbours; zero elsewhere."""
         import torch
         pc = full[::4, ::4]
         tc = min(float(torch.quantile(pc.reshape(-1).float(), 0.8).item()), tau)
-        keep = _grow(pc >= tc).repeat_interleave(4, 0).repeat_interleave(4, 1)[:full.shape[0], :full.shape[1]]
+        flag = pc >= tc
+        if near_coarse is not None:
+            flag = flag | near_coarse
+        keep = _grow(flag).repeat_interleave(4, 0).repeat_interleave(4, 1)[:full.shape[0], :full.shape[1]]
         return torch.where(keep, full, torch.zeros_like(full))
+
+    def coarse_near(self, ctx: MatrixContext, grid: Grid):
+        """near_curve of the hierarchical pass's coarse anchors, as a (ny/4, nx/4) map."""
+        import torch
+        dev = ctx.bands.device
+        ic = torch.arange(0, grid.ny, 4, device=dev, dtype=torch.int32)
+        jc = torch.arange(0, grid.nx, 4, device=dev, dtype=torch.int32)
+        cidx = (ic[:, None] * grid.nx + jc[None, :]).reshape(-1).contiguous()
+        xc = point_features(ctx, grid, cidx)
+        return near_curve(xc, grid, self.eps, coarse=True).view(ic.numel(), jc.numel())
 
     def calibrate(self, ctxs, grids, sig_truth: List[np.ndarray], taus=None, hierarchical: bool = True,
                   target: float = TARGET_RECALL):
@@ -346,19 +384,23 @@ class Restriction:
         target; also the paper's literal rule (smallest tau with median recall >= 0.9
         and 10th-percentile recall >= 0.75) for reference."""
         import torch
-        taus = list(np.round(np.arange(0.01, 1.0, 0.01), 2)) if taus is None else list(taus)
+        if taus is None:
+            taus = list(np.round(np.arange(0.001, 0.01, 0.001), 3)) + list(np.round(np.arange(0.01, 1.0, 0.01), 2))
+        taus = list(taus)
         full = [self.predict(c, g, hierarchical=False) for c, g in zip(ctxs, grids)]
-        table = []
+        nearc = [self.coarse_near(c, g) for c, g in zip(ctxs, grids)]
+        table, per_matrix = [], []
         for t in taus:
             recs, fracs, recs_full = [], [], []
-            for pf, g, s in zip(full, grids, sig_truth):
-                p = self.hierarchical_mask(pf, t) if hierarchical else pf
+            for pf, nc, g, s in zip(full, nearc, grids, sig_truth):
+                p = self.hierarchical_mask(pf, t, nc) if hierarchical else pf
                 r = region_mask(p.reshape(-1).contiguous(), g, t).cpu().numpy().astype(bool)
                 mtr = recall_metrics(s <= self.eps, r)
                 recs.append(mtr["recall"])
                 fracs.append(mtr["grid_fraction"])
                 rf = region_mask(pf.reshape(-1).contiguous(), g, t).cpu().numpy().astype(bool)
                 recs_full.append(recall_metrics(s <= self.eps, rf)["recall"])
+            per_matrix.append(recs)
             table.append({"tau": float(t), "min_recall": float(np.min(recs)), "median_recall": float(np.median(recs)),
                           "p10_recall": float(np.percentile(recs, 10)), "mean_grid_fraction": float(np.mean(fracs)),
                           "min_recall_without_hierarchy": float(np.min(recs_full))})
@@ -366,9 +408,11 @@ class Restriction:
         chosen = max(ok, key=lambda r: r["tau"]) if ok else min(table, key=lambda r: r["tau"])
         paper = [row for row in table if row["median_recall"] >= 0.9 and row["p10_recall"] >= 0.75]
         self.tau = chosen["tau"]
+        recs = per_matrix[taus.index(chosen["tau"])]
         self.calibration = {"tau": self.tau, "target_recall": target, "row": chosen,
                             "paper_rule_tau": min(r["tau"] for r in paper) if paper else None,
-                            "matrices": len(grids), "table": table}
+                            "matrices": len(grids), "per_matrix_recall": [float(r) for r in recs],
+                            "worst_matrix": int(np.argmin(recs)), "table": table}
         return self.calibration
 
     # --------------------------------------------------------- restricted run

@@ -24,7 +24,7 @@ def _blocks(theta):
         o, r, c = mlp.DUAL_BLOCKS[name]
         return theta[o:o + r * c].view(r, c)
     WA, bA, WB, bB = blk("WA"), blk("bA")[:, 0], blk("WB"), blk("bB")[:, 0]
-    return {"Wc1": WA[0:64, 0:26], "bc1": bA[0:64], "Wm1": WA[64:192, 26:60], "bm1": bA[64:192],
+    return {"Wc1": WA[0:64, 0:26], "bc1": bA[0:64], "Wm1": WA[64:192, 26:61], "bm1": bA[64:192],
             "Wc2": WB[0:64, 0:64], "bc2": bB[0:64], "Wm2": WB[64:128, 64:192], "bm2": bB[64:128],
             "W4": blk("W4"), "b4": blk("b4")[:, 0], "W5": blk("W5"), "b5": blk("b5")[:, 0],
             "W7": blk("W7")[0:64], "b7": blk("b7")[0:64, 0], "w8": blk("w8")[0:64, 0], "b8": blk("b8")[0, 0]}
@@ -36,7 +36,7 @@ def _ref_forward(theta, x):
     silu = torch.nn.functional.silu
     lin = lambda h, W, b: h @ bf(W).T + b
     x = x.float()
-    phi, f = x[:, 0:26], x[:, 26:60]
+    phi, f = x[:, 0:26], x[:, 26:61]
     hc = bf(silu(lin(bf(silu(lin(phi, p["Wc1"], p["bc1"]))), p["Wc2"], p["bc2"])))
     hm = bf(silu(lin(bf(silu(lin(f, p["Wm1"], p["bm1"]))), p["Wm2"], p["bm2"])))
     h3 = torch.cat([hc, hm], dim=1)
@@ -57,8 +57,8 @@ def _theta(seed):
 
 def test_parameter_count_matches_the_architecture():
     m = mlp.dual_param_mask()
-    # 26*64+64 + 64*64+64 + 34*128+128 + 128*64+64 + 2*(128*128+128) + 128*64+64 + 64+1
-    assert int(m.sum()) == mlp._native.DUAL_TRAINABLE == 59969
+    # 26*64+64 + 64*64+64 + 35*128+128 + 128*64+64 + 2*(128*128+128) + 128*64+64 + 64+1
+    assert int(m.sum()) == mlp._native.DUAL_TRAINABLE == 60097
 
 
 @pytest.mark.parametrize("rows", [1, 130, 1000])
@@ -77,7 +77,7 @@ def test_columns_past_the_features_are_ignored():
     g = torch.Generator(device=DEV).manual_seed(3)
     x = torch.randn(300, mlp.IN, device=DEV, generator=g)
     x2 = x.clone()
-    x2[:, 60:] = 7.0
+    x2[:, 61:] = 7.0
     p1 = mlp.forward(theta, x.to(torch.bfloat16), net="dual")
     p2 = mlp.forward(theta, x2.to(torch.bfloat16), net="dual")
     torch.cuda.synchronize()

@@ -98,12 +98,23 @@ def test_point_features_match_numpy():
             ref += [np.sin(w * cx), np.sin(w * cy), np.cos(w * cx), np.cos(w * cy)]
         d = np.abs(sym - z)
         ang = np.angle(np.roll(sym - z, -1) / (sym - z)).sum()
-        ref += [d.min() / R, abs(z - cen) / R, d.mean() / R, np.log10(d.min() / R + 1e-7),
+        # distance to the closed polyline through the samples: the nearest point of each
+        # piece s_{k-1} -> s_k
+        s0, s1 = np.roll(sym, 1), sym
+        e = s1 - s0
+        t = np.clip(np.real(np.conj(e) * (z - s0)) / np.maximum(np.abs(e) ** 2, 1e-300), 0.0, 1.0)
+        dpoly = np.abs(s0 + t * e - z).min()
+        assert dpoly <= d.min()
+        ref += [dpoly / R, abs(z - cen) / R, d.mean() / R, np.log10(dpoly / R + 1e-7),
                 np.log10(d.mean() / R + 1e-7), np.rint(ang / (2 * np.pi))]
         # BF16 rows: 8 significant bits
         np.testing.assert_allclose(x[f, :32], np.array(ref), rtol=1e-2, atol=2e-2)
-        np.testing.assert_allclose(x[f, 32:32 + _native.GLOBAL_FEATURES], ctx.glob.cpu().numpy(), rtol=1e-2, atol=1e-3)
-        assert np.all(x[f, 32 + _native.GLOBAL_FEATURES:] == 0)
+        gl = ctx.glob.cpu().numpy()
+        np.testing.assert_allclose(x[f, 32:32 + _native.GLOBAL_FEATURES], gl, rtol=1e-2, atol=1e-3)
+        # log10(distance / eps), with gl[24] = log10(eps / R)
+        np.testing.assert_allclose(x[f, 32 + _native.GLOBAL_FEATURES], np.log10(dpoly / R + 1e-7) - gl[24],
+                                   rtol=1e-2, atol=2e-2)
+        assert np.all(x[f, 33 + _native.GLOBAL_FEATURES:] == 0)
 
 
 def test_region_and_tile_list_match_numpy():
@@ -124,9 +135,29 @@ def test_hierarchical_map_is_masked_full_map():
     r = restriction.Restriction(DEV, seed=1)
     grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 42, 30)
     full = r.predict(ctx, grid, hierarchical=False)
+    nc = r.coarse_near(ctx, grid)
+    assert nc.any()  # the Grcar symbol curve crosses this grid
     for tau in (0.2, 0.5, 0.8):
         h = r.predict(ctx, grid, hierarchical=True, tau=tau)
-        torch.testing.assert_close(h, restriction.Restriction.hierarchical_mask(full, tau), rtol=0, atol=0)
+        torch.testing.assert_close(h, restriction.Restriction.hierarchical_mask(full, tau, nc), rtol=0, atol=0)
+
+
+def test_points_near_the_symbol_curve_enter_the_region():
+    """A nearly normal band (kl = ku Grcar-type: A - I is skew-symmetric, plus 1e-3 noise)
+    has a sensitive zone of width about 2 eps along its spectrum, the symbol segment:
+    every sensitive point gets probability 1 from the near-curve rule, whatever the
+    network says (an untrained network here)."""
+    rng = np.random.default_rng(4)
+    b = inputs.grcar_type(3000, 1, 1)
+    b = b + 1e-3 * (rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape))
+    grid = inputs.toeplitz_symbol_grid(np.array([-1.0, 1.0, 1.0], dtype=np.complex128), 1, 1, 97, 96, min_aspect=0.5)
+    bt = _t(b)
+    ctx = restriction.matrix_contexts([(bt, 1, 1)])[0]
+    r = restriction.Restriction(DEV, seed=3)
+    p = r.predict(ctx, grid, hierarchical=True, tau=0.5).cpu().numpy()
+    sig = psa.sigma_min(bt, 1, 1, grid).sigma.cpu().numpy()
+    sens = sig <= restriction.EPS
+    assert sens.sum() >= 20 and np.all(p[sens] == 1.0)
 
 
 def test_small_end_to_end_pipeline():
@@ -162,13 +193,16 @@ def test_small_end_to_end_pipeline():
     assert met["recall"] >= 0.5, met
 
 
-def test_shipped_classifier_reaches_recall_on_a_fresh_matrix():
-    """The classifier shipped with the package (trained on 2000 seeded matrices) on a
-    matrix outside its training set: recall against the 3x3-dilated truth >= 0.99,
-    sigma on the region bitwise equal to the full grid."""
+@pytest.mark.parametrize("net", ["mlp", "dual"])
+def test_shipped_classifier_reaches_recall_on_a_fresh_matrix(net):
+    """The classifiers shipped with the package (the MLP and the paper's dual-path net,
+    trained on the same labels of 2000 seeded matrices, thresholds calibrated above the
+    grid minimum) on matrices outside their training set: recall against the
+    3x3-dilated truth >= 0.99, sigma on the region bitwise equal to the full grid."""
     import os
-    path = os.path.join(os.path.dirname(restriction.__file__), "data", "restriction_mlp.npz")
+    path = os.path.join(os.path.dirname(restriction.__file__), "data", f"restriction_{net}.npz")
     r = restriction.Restriction.load(path, DEV)
+    assert r.net == net and r.tau > 0.01 and r.calibration["row"]["min_recall"] >= 0.99
     for n, kl, ku, nx, ny, seed in ((600, 2, 4, 64, 48, 9), (1500, 3, 6, 96, 80, 31)):
         b, kl, ku, g = inputs.restriction_test_matrix(n=n, kl=kl, ku=ku, nx=nx, ny=ny, seed=seed)
         bt = _t(b)
