@@ -771,6 +771,9 @@ def run_restriction(args):
     bt = torch.as_tensor(b, device=dev)
     opts = psa.LanczosOpts(k_min=2, k_max=KMAX, tol=TOL)
     pif = psa.default_points_in_flight(bt.shape[1], kl, ku, grid.npoints)
+    free, _ = torch.cuda.mem_get_info(dev)
+    while pif > 32 * 4 and psa.workspace_bytes(bt.shape[1], kl, ku, pif, opts, grid.npoints) > 0.75 * free:
+        pif //= 2  # a large order: fewer points in flight so that the workspace fits with room to spare
     wsp = psa.Workspace(bt.shape[1], kl, ku, pif, opts, device=dev, npoints=grid.npoints)
     small = inp.Grid(grid.re_min, grid.re_max, grid.im_min, grid.im_max, 64, 64)
     psa.sigma_min(bt, kl, ku, small, eps=EPS, opts=opts, workspace=wsp)  # warm-up: modules and workspace
