@@ -65,6 +65,9 @@ SMALL = dict(n=256, nx=384, ny=384, kmax=300)
 
 
 def workload(case: str = "mid"):
+    if case == "grcar100":  # the first workload: Grcar n = 100 on its 100 x 100 grid
+        bands, kl, ku = inputs.grcar(100)
+        return bands, kl, ku, inputs.grcar_grid_100()
     n, nx, ny = (N, NX, NY) if case == "mid" else (SMALL["n"], SMALL["nx"], SMALL["ny"])
     bands, kl, ku, a = inputs.random_toeplitz(n, KL, KU, seed=SEED)
     grid = inputs.toeplitz_symbol_grid(a, kl, ku, nx, ny)
@@ -351,7 +354,7 @@ def run_gpu(args):
     n = bands.shape[1]
     npts = grid.npoints
     b_dev = torch.as_tensor(bands, device=dev)
-    opts = psa.LanczosOpts(k_min=2, k_max=KMAX if args.case == "mid" else SMALL["kmax"], tol=TOL, seed=0)
+    opts = psa.LanczosOpts(k_min=2, k_max=SMALL["kmax"] if args.case == "small" else KMAX, tol=TOL, seed=0)
     pif = psa.default_points_in_flight(n, kl, ku, npts)
     wsp = psa.Workspace(n, kl, ku, pif, opts, device=dev, npoints=npts)
     out = psa.sigma_min(b_dev, kl, ku, grid, eps=EPS, opts=opts, workspace=wsp)
@@ -645,20 +648,22 @@ def run_batched(args):
 
     # end to end: bands from pinned host memory into the plan's device tensors, the
     # graph, sigma and masks back to pinned host memory
-    pinned = [torch.as_tensor(b).pin_memory() for b, *_ in w]
+    e2e = None
+    pinned = [] if args.no_e2e else [torch.as_tensor(b).pin_memory() for b, *_ in w]
     h_sigma = torch.empty(npts, dtype=torch.float64).pin_memory()
     h_mask = torch.empty(npts, dtype=torch.int32).pin_memory()
     torch.cuda.synchronize(dev)
-    t1 = time.perf_counter()
-    for hb, (db, *_r) in zip(pinned, mats):
-        db.copy_(hb, non_blocking=True)
-    out = g.replay()
-    h_sigma.copy_(out.sigma, non_blocking=True)
-    h_mask.copy_(out.mask, non_blocking=True)
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t1
-    e2e = {"value": npts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sum(b.nbytes for b, *_ in w)),
-           "d2h_bytes_per_step": int(npts * 12)}
+    if not args.no_e2e:
+        t1 = time.perf_counter()
+        for hb, (db, *_r) in zip(pinned, mats):
+            db.copy_(hb, non_blocking=True)
+        out = g.replay()
+        h_sigma.copy_(out.sigma, non_blocking=True)
+        h_mask.copy_(out.mask, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t1
+        e2e = {"value": npts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sum(b.nbytes for b, *_ in w)),
+               "d2h_bytes_per_step": int(npts * 12)}
     ns = np.array([b.shape[1] for b, *_ in w])
     line = {"workload": "batched", "metric": METRIC, "value": npts / (mean_ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
@@ -932,8 +937,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="mid", choices=["mid", "small"],
-                    help="mid: the benchmark workload; small: reduced case for profiler captures")
+    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100"],
+                    help="mid: the benchmark workload; small: reduced case for profiler captures; "
+                         "grcar100: the Grcar n = 100 workload (small-order profile)")
     ap.add_argument("--workload", default="grid",
                     choices=["grid", "differentiation", "batched", "restriction", "classifier"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
@@ -951,6 +957,7 @@ def main():
                     help="restriction: load trained classifier(s) (comma-separated .npz, one per network) "
                          "instead of training")
     ap.add_argument("--no-tune", action="store_true", help="batched: default launch controls")
+    ap.add_argument("--no-e2e", action="store_true", help="batched: skip the end-to-end replay")
     ap.add_argument("--batch-streams", type=int, default=8, help="batched with --no-tune: streams")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps

@@ -206,6 +206,24 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
                        int8_t *status, int32_t *steps, const psa_lanczos_opts *opts,
                        void *workspace, size_t ws_bytes, void *stream);
 
+/* psa_sigma_min_grad without the band gradient, writing instead the singular
+ * pair of every point, element-major: u[i * n_pts + p] and v[i * n_pts + p]
+ * (DEVICE, n * n_pts complex each; B v = sigma u, |u| = |v| = 1, the phases
+ * those of the kernel's Ritz vector; zeros where grad_z is 0). A backward pass
+ * that learns its weights later then needs only psa_band_grad_from_pairs.
+ * Other arguments and errors as psa_sigma_min_grad. */
+int psa_sigma_min_pairs(const psa_band *A, const psa_c64 *z, int64_t n_pts, double *sigma, psa_c64 *grad_z,
+                        psa_c64 *u, psa_c64 *v, int8_t *status, int32_t *steps, const psa_lanczos_opts *opts,
+                        void *workspace, size_t ws_bytes, void *stream);
+
+/* grad_bands[(d + kl) * n + i] = -sum_p weight[p] u_p[i] conj(v_p[i + d]), the
+ * weighted band gradient of psa_sigma_min_grad, from stored singular pairs
+ * (layout of psa_sigma_min_pairs; A's bands pointer is not read). One warp per
+ * band entry with a fixed-order sum: the same bits on every run. DEVICE
+ * pointers; asynchronous on stream. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_band_grad_from_pairs(const psa_band *A, int64_t n_pts, const psa_c64 *u, const psa_c64 *v,
+                             const double *weight, psa_c64 *grad_bands, void *stream);
+
 /* Size of the fixed device scratch used by psa_sigma_min_static (64 MiB). */
 #define PSA_STATIC_SCRATCH_BYTES (64u << 20)
 

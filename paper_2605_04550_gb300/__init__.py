@@ -28,6 +28,7 @@ __all__ = [
     "Grid", "LanczosOpts", "SigmaMinResult", "Workspace", "sigma_min", "workspace_bytes",
     "default_points_in_flight", "probe_dfma_rate", "library_path", "PsaError", "tile_order",
     "SigmaMinGradResult", "sigma_min_grad", "grad_workspace_bytes", "SigmaMinFunction", "sigma_min_autograd",
+    "GradWorkspace", "band_grad_from_pairs", "release_workspaces",
     "PT_OK", "PT_SINGULAR", "PT_NOT_CONVERGED", "PT_NONFINITE", "PT_NOT_EVALUATED", "PT_UNDERFLOW",
 ]
 
@@ -111,6 +112,26 @@ class Workspace:
         self.ptr = base + self.offset
 
 
+# The workspace of the last sigma_min call made without one, per device: repeated calls
+# on the same problem shape reuse it instead of allocating; release_workspaces() frees it.
+_default_ws = {}
+
+
+def _default_workspace(n: int, kl: int, ku: int, pif: int, o: "LanczosOpts", dev, npoints: int) -> Workspace:
+    key = (n, kl, ku, pif, o.k_max, npoints)
+    ent = _default_ws.get(str(dev))
+    if ent is None or ent[0] != key:
+        _default_ws.pop(str(dev), None)  # free the old buffer before taking the new one
+        ent = (key, Workspace(n, kl, ku, pif, o, device=dev, npoints=npoints))
+        _default_ws[str(dev)] = ent
+    return ent[1]
+
+
+def release_workspaces() -> None:
+    """Free the workspaces that sigma_min keeps for calls made without one (the memory
+    returns to torch's caching allocator)."""
+    _default_ws.clear()
+
 
 def _check_out(out, npoints: int, dev) -> None:
     """Caller-provided outputs: contiguous, on the device, one entry per grid point."""
@@ -129,6 +150,10 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
 
     bands: CUDA complex128 (kl + ku + 1, n), bands[d + kl, i] = A[i, i + d].
     idx:   optional CUDA int32 tensor of flat grid indices (restricted mode).
+    workspace: a Workspace to use; without one, the binding keeps the workspace of the
+    last such call per device and reuses it for calls of the same shape (the size fills
+    the device once: up to tens of GB at large n; ``release_workspaces()`` frees it).
+    Calls that may overlap on the GPU must not share a workspace: pass each its own.
     Asynchronous on ``stream`` (default: torch's current stream).
     """
     import torch
@@ -145,7 +170,7 @@ def sigma_min(bands, kl: int, ku: int, grid: Grid, eps: Sequence[float] = (), id
     o = opts or LanczosOpts()
     if workspace is None:
         pif = points_in_flight or default_points_in_flight(n, kl, ku, max(npts, 1))
-        workspace = Workspace(n, kl, ku, pif, o, device=dev, npoints=npts)
+        workspace = _default_workspace(n, kl, ku, pif, o, dev, npts)
     elif points_in_flight is not None:
         raise ValueError("pass either workspace or points_in_flight")
     if out is None:
@@ -178,6 +203,8 @@ class SigmaMinGradResult:
     grad_bands: "object"  # torch.complex128 (kl + ku + 1, n) or None
     status: "object"      # torch.int8 (npts,)
     steps: "object"       # torch.int32 (npts,)
+    u: "object" = None    # torch.complex128 (n, npts) singular vectors (pairs=True), element-major
+    v: "object" = None
 
 
 def grad_workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
@@ -190,12 +217,28 @@ def grad_workspace_bytes(n: int, kl: int, ku: int, points_in_flight: int,
     return int(out.value)
 
 
+class GradWorkspace:
+    """Reusable device workspace of psa_sigma_min_grad / psa_sigma_min_pairs."""
+
+    def __init__(self, n: int, kl: int, ku: int, points_in_flight: int, opts: Optional[LanczosOpts] = None,
+                 device="cuda"):
+        import torch
+        self.nbytes = grad_workspace_bytes(n, kl, ku, points_in_flight, opts)
+        self._buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        self.ptr = self._buf.data_ptr() + ((-self._buf.data_ptr()) % 256)
+        self.shape = (int(n), int(kl), int(ku), (opts or LanczosOpts()).k_max)
+
+
 def sigma_min_grad(bands, kl: int, ku: int, z, weight=None, opts: Optional[LanczosOpts] = None,
-                   points_in_flight: Optional[int] = None, stream=None) -> SigmaMinGradResult:
+                   points_in_flight: Optional[int] = None, stream=None, workspace: Optional[GradWorkspace] = None,
+                   pairs: bool = False) -> SigmaMinGradResult:
     """sigma_min(z I - A) at explicit points with its adjoint gradients (psa_sigma_min_grad).
 
     z: CUDA complex128 tensor of points. weight: optional CUDA float64 tensor of
     upstream weights; when given, grad_bands = sum_p weight_p d sigma_p / d bands.
+    workspace: a GradWorkspace to reuse (else one is allocated for this call).
+    pairs: also return the singular pair of every point (psa_sigma_min_pairs; then no
+    weight): u, v as (n, npts) complex tensors, element-major.
     """
     import torch
     lib = _native.load()
@@ -211,22 +254,55 @@ def sigma_min_grad(bands, kl: int, ku: int, z, weight=None, opts: Optional[Lancz
         weight = weight.to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
         if weight.numel() != npts:
             raise ValueError("weight must have one entry per point")
-    pif = points_in_flight or min(default_points_in_flight(n, kl, ku, max(npts, 1)), max(32, -(-npts // 32) * 32))
-    nbytes = grad_workspace_bytes(n, kl, ku, pif, o)
-    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
-    ptr = buf.data_ptr() + ((-buf.data_ptr()) % 256)
+    if pairs and weight is not None:
+        raise ValueError("pairs=True returns the singular pairs instead of a band gradient: pass no weight")
+    if workspace is None:
+        pif = points_in_flight or min(default_points_in_flight(n, kl, ku, max(npts, 1)),
+                                      max(32, -(-npts // 32) * 32))
+        workspace = GradWorkspace(n, kl, ku, pif, o, device=dev)
+    elif points_in_flight is not None:
+        raise ValueError("pass either workspace or points_in_flight")
+    elif workspace.shape[:3] != (n, int(kl), int(ku)) or workspace.shape[3] < o.k_max:
+        raise ValueError("workspace was sized for another problem")
+    nbytes, ptr = workspace.nbytes, workspace.ptr
     sigma = torch.empty(npts, dtype=torch.float64, device=dev)
     gz = torch.empty(npts, dtype=torch.complex128, device=dev)
     gb = torch.empty((kl + ku + 1, n), dtype=torch.complex128, device=dev) if weight is not None else None
     status = torch.empty(npts, dtype=torch.int8, device=dev)
     steps = torch.empty(npts, dtype=torch.int32, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    if pairs:
+        u = torch.empty((n, npts), dtype=torch.complex128, device=dev)
+        v = torch.empty((n, npts), dtype=torch.complex128, device=dev)
+        rc = lib.psa_sigma_min_pairs(ctypes.byref(A), zc.data_ptr() if npts else None, npts, sigma.data_ptr(),
+                                     gz.data_ptr(), u.data_ptr() if npts else None, v.data_ptr() if npts else None,
+                                     status.data_ptr(), steps.data_ptr(), ctypes.byref(o._c()), ptr, nbytes,
+                                     s.cuda_stream)
+        _native.check(rc, "psa_sigma_min_pairs")
+        return SigmaMinGradResult(sigma, gz, None, status, steps, u, v)
     rc = lib.psa_sigma_min_grad(ctypes.byref(A), zc.data_ptr() if npts else None, npts,
                                 weight.data_ptr() if weight is not None else None,
                                 sigma.data_ptr(), gz.data_ptr(), gb.data_ptr() if gb is not None else None,
                                 status.data_ptr(), steps.data_ptr(), ctypes.byref(o._c()), ptr, nbytes, s.cuda_stream)
     _native.check(rc, "psa_sigma_min_grad")
     return SigmaMinGradResult(sigma, gz, gb, status, steps)
+
+
+def band_grad_from_pairs(n: int, kl: int, ku: int, u, v, weight, stream=None):
+    """Weighted band gradient -sum_p w_p u_p[i] conj(v_p[i + d]) from stored singular pairs
+    (psa_band_grad_from_pairs); u, v (n, npts) complex128, weight (npts,) float64."""
+    import torch
+    lib = _native.load()
+    npts = int(u.shape[1])
+    if u.shape != (n, npts) or v.shape != (n, npts) or weight.numel() != npts:
+        raise ValueError("u, v must be (n, npts) and weight (npts,)")
+    w = weight.to(dtype=torch.float64).contiguous().reshape(-1)
+    gb = torch.empty((kl + ku + 1, n), dtype=torch.complex128, device=u.device)
+    s = stream if stream is not None else torch.cuda.current_stream(u.device)
+    _native.check(lib.psa_band_grad_from_pairs(ctypes.byref(_band_shape(n, kl, ku)), npts, u.data_ptr(),
+                                               v.data_ptr(), w.data_ptr(), gb.data_ptr(), s.cuda_stream),
+                  "psa_band_grad_from_pairs")
+    return gb
 
 
 def tile_order(flat_idx, nx: int):
@@ -253,35 +329,49 @@ def probe_dfma_rate(iters: int = 4096, stream=None) -> float:
     return float(out.value)
 
 
+#: bytes of singular pairs (2 * 16 * n * points) the autograd forward keeps for its backward
+PAIR_BUDGET = 2 << 30
+
+
 def _make_autograd():
     import torch
 
     class SigmaMinFunction(torch.autograd.Function):
         """sigma_min(z I - A) as a differentiable function of the band entries and z.
 
-        forward(bands, z, kl, ku, opts) -> sigma (float64, shape of z); backward uses the
-        adjoint kernel (psa_sigma_min_grad) with the upstream gradient as weights:
-        d/d bands = sum_p g_p d sigma_p / d bands, d/d z_p = g_p d sigma_p / d z
-        (PyTorch's convention for complex inputs: d/d Re + i d/d Im).
+        forward(bands, z, kl, ku, opts) -> sigma (float64, shape of z); backward forms
+        d/d bands = sum_p g_p d sigma_p / d bands and d/d z_p = g_p d sigma_p / d z
+        (PyTorch's convention for complex inputs: d/d Re + i d/d Im). When the bands
+        need a gradient and the singular pairs of all points fit in PAIR_BUDGET bytes,
+        the forward keeps them (psa_sigma_min_pairs) and the backward is one contraction
+        (psa_band_grad_from_pairs); otherwise the backward reruns the adjoint kernel
+        (psa_sigma_min_grad) with the upstream gradient as weights.
         """
 
         @staticmethod
         def forward(ctx, bands, z, kl, ku, opts=None):
-            r = sigma_min_grad(bands.detach(), kl, ku, z.detach(), weight=None, opts=opts)
-            ctx.save_for_backward(bands.detach(), z.detach(), r.grad_z)
-            ctx.kl, ctx.ku, ctx.opts = kl, ku, opts
+            n, npts = int(bands.shape[1]), int(z.numel())
+            keep = bands.requires_grad and 2 * 16 * n * npts <= PAIR_BUDGET
+            r = sigma_min_grad(bands.detach(), kl, ku, z.detach(), weight=None, opts=opts, pairs=keep)
+            if keep:
+                ctx.save_for_backward(r.u, r.v, r.grad_z)
+            else:
+                ctx.save_for_backward(bands.detach(), z.detach(), r.grad_z)
+            ctx.kl, ctx.ku, ctx.opts, ctx.keep, ctx.n = kl, ku, opts, keep, n
             return r.sigma.reshape(z.shape)
 
         @staticmethod
         def backward(ctx, g):
-            bands, z, gz = ctx.saved_tensors
+            a, b, gz = ctx.saved_tensors
             gflat = g.reshape(-1).to(torch.float64).contiguous()
             grad_bands = grad_z = None
             if ctx.needs_input_grad[0]:
-                r = sigma_min_grad(bands, ctx.kl, ctx.ku, z, weight=gflat, opts=ctx.opts)
-                grad_bands = r.grad_bands
+                if ctx.keep:
+                    grad_bands = band_grad_from_pairs(ctx.n, ctx.kl, ctx.ku, a, b, gflat)
+                else:
+                    grad_bands = sigma_min_grad(a, ctx.kl, ctx.ku, b, weight=gflat, opts=ctx.opts).grad_bands
             if ctx.needs_input_grad[1]:
-                grad_z = (gz * gflat).reshape(z.shape)
+                grad_z = (gz * gflat).reshape(g.shape)
             return grad_bands, grad_z, None, None, None
 
     return SigmaMinFunction

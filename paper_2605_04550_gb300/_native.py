@@ -28,6 +28,8 @@ EXPORTS = (
     "psa_sigma_min_static",
     "psa_grad_workspace_bytes",
     "psa_sigma_min_grad",
+    "psa_sigma_min_pairs",
+    "psa_band_grad_from_pairs",
     "psa_batch_plan_bytes",
     "psa_batch_plan",
     "psa_batch_workspace_bytes",
@@ -123,6 +125,11 @@ def load(path: str | None = None):
         lib.psa_sigma_min_grad.restype = ctypes.c_int
         lib.psa_sigma_min_grad.argtypes = [ctypes.POINTER(PsaBand), vp, i64, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
+        lib.psa_sigma_min_pairs.restype = ctypes.c_int
+        lib.psa_sigma_min_pairs.argtypes = [ctypes.POINTER(PsaBand), vp, i64, vp, vp, vp, vp, vp, vp,
+                                            ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
+        lib.psa_band_grad_from_pairs.restype = ctypes.c_int
+        lib.psa_band_grad_from_pairs.argtypes = [ctypes.POINTER(PsaBand), i64, vp, vp, vp, vp, vp]
         lib.psa_batch_plan_bytes.restype = ctypes.c_int
         lib.psa_batch_plan_bytes.argtypes = [i32, ctypes.POINTER(ctypes.c_size_t)]
         lib.psa_batch_plan.restype = ctypes.c_int

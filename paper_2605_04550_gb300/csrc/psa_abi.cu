@@ -474,9 +474,46 @@ int psa_grad_workspace_bytes(const psa_band *A, const psa_lanczos_opts *opts, in
     return PSA_OK;
 }
 
-int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const double *weight, double *sigma,
-                       psa_c64 *grad_z, psa_c64 *grad_bands, int8_t *status, int32_t *steps,
-                       const psa_lanczos_opts *opts, void *workspace, size_t ws_bytes, void *stream_ptr)
+}  // extern "C"
+
+namespace psa {
+namespace {
+
+// grad_bands[(d + kl) * n + i] = -sum_p w[p] u[i][p] conj(v[i + d][p]): one warp per band
+// entry, its lanes striding over the points (element-major u, v: coalesced reads),
+// then a fixed-order shuffle sum (the same bits on every run).
+__global__ void k_band_grad_pairs(int n, int kl, int ku, int64_t npts, const double2 *u, const double2 *v,
+                                  const double *w, double2 *g)
+{
+    const int64_t nent = (int64_t)(kl + ku + 1) * n;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nent;
+         e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int dk = (int)(e / n), i = (int)(e - (int64_t)dk * n);
+        const int j = i + dk - kl;
+        double gx = 0.0, gy = 0.0;
+        if (j >= 0 && j < n) {
+            const double2 *ui = u + (int64_t)i * npts, *vj = v + (int64_t)j * npts;
+            for (int64_t q = lane; q < npts; q += 32) {
+                const double2 a = ui[q], b = vj[q];
+                const double c = -w[q];
+                gx = fma(c, fma(a.x, b.x, a.y * b.y), gx);
+                gy = fma(c, fma(a.y, b.x, -(a.x * b.y)), gy);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, off);
+            gy += __shfl_xor_sync(0xffffffffu, gy, off);
+        }
+        if (lane == 0) g[e] = make_double2(gx, gy);
+    }
+}
+
+int sigma_min_grad_impl(const psa_band *A, const psa_c64 *z, int64_t n_pts, const double *weight, double *sigma,
+                        psa_c64 *grad_z, psa_c64 *grad_bands, psa_c64 *u_out, psa_c64 *v_out, int8_t *status,
+                        int32_t *steps, const psa_lanczos_opts *opts, void *workspace, size_t ws_bytes,
+                        void *stream_ptr)
 {
     if (!band_ok(A) || !A->bands || n_pts < 0 || (n_pts > 0 && (!z || !sigma))) return PSA_EINVAL;
     if (grad_bands && !weight) return PSA_EINVAL;
@@ -519,6 +556,8 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
     p.gweight = weight;
     p.grad_z = reinterpret_cast<double2 *>(grad_z);
     p.grad_bands = reinterpret_cast<double2 *>(grad_bands);
+    p.u_out = reinterpret_cast<double2 *>(u_out);
+    p.v_out = reinterpret_cast<double2 *>(v_out);
     p.sigma = sigma;
     p.status = status;
     p.steps = steps;
@@ -548,6 +587,45 @@ int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const
     if (n_pts == 0) return PSA_OK;
     if (ops.launch(p, stream) != cudaSuccess) return PSA_ECUDA;
     return PSA_OK;
+}
+
+}  // namespace
+}  // namespace psa
+
+extern "C" {
+
+int psa_sigma_min_grad(const psa_band *A, const psa_c64 *z, int64_t n_pts, const double *weight, double *sigma,
+                       psa_c64 *grad_z, psa_c64 *grad_bands, int8_t *status, int32_t *steps,
+                       const psa_lanczos_opts *opts, void *workspace, size_t ws_bytes, void *stream_ptr)
+{
+    return sigma_min_grad_impl(A, z, n_pts, weight, sigma, grad_z, grad_bands, nullptr, nullptr, status, steps,
+                               opts, workspace, ws_bytes, stream_ptr);
+}
+
+int psa_sigma_min_pairs(const psa_band *A, const psa_c64 *z, int64_t n_pts, double *sigma, psa_c64 *grad_z,
+                        psa_c64 *u, psa_c64 *v, int8_t *status, int32_t *steps, const psa_lanczos_opts *opts,
+                        void *workspace, size_t ws_bytes, void *stream_ptr)
+{
+    if (n_pts > 0 && (!u || !v)) return PSA_EINVAL;
+    return sigma_min_grad_impl(A, z, n_pts, nullptr, sigma, grad_z, nullptr, n_pts > 0 ? u : nullptr, v, status,
+                               steps, opts, workspace, ws_bytes, stream_ptr);
+}
+
+int psa_band_grad_from_pairs(const psa_band *A, int64_t n_pts, const psa_c64 *u, const psa_c64 *v,
+                             const double *weight, psa_c64 *grad_bands, void *stream_ptr)
+{
+    if (!band_ok(A) || n_pts < 0 || !grad_bands || (n_pts > 0 && (!u || !v || !weight))) return PSA_EINVAL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const int64_t nent = (int64_t)(A->kl + A->ku + 1) * A->n;
+    if (n_pts == 0)
+        return cudaMemsetAsync(grad_bands, 0, sizeof(psa_c64) * (size_t)nent, stream) == cudaSuccess ? PSA_OK
+                                                                                                     : PSA_ECUDA;
+    const int64_t blocks = (nent * 32 + 255) / 256 < 65536 ? (nent * 32 + 255) / 256 : 65536;
+    k_band_grad_pairs<<<(unsigned)blocks, 256, 0, stream>>>(A->n, A->kl, A->ku, n_pts,
+                                                            reinterpret_cast<const double2 *>(u),
+                                                            reinterpret_cast<const double2 *>(v), weight,
+                                                            reinterpret_cast<double2 *>(grad_bands));
+    return cudaGetLastError() == cudaSuccess ? PSA_OK : PSA_ECUDA;
 }
 
 // ------------------------------------------------------------------ batches

@@ -20,7 +20,9 @@
 //      vectors as eigenvectors), v = B^{-1} u / |B^{-1} u|;
 //   4. grad_z = sum_i u_i conj(v_i); for every band entry (i, i+d) the weighted
 //      contribution -w u_i conj(v_{i+d}) is summed over the warp's 32 points with
-//      shuffles and added to grad_bands with one atomic per entry and warp.
+//      shuffles and added to grad_bands with one atomic per entry and warp;
+//   5. optionally u and v themselves are written out, so that band gradients for
+//      other weights later need only the contraction k_band_grad_pairs.
 #pragma once
 #include "psa_kernel.cuh"
 
@@ -189,6 +191,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
                 gz.x *= inv_nx;
                 gz.y *= inv_nx;
                 wgt = p.gweight ? p.gweight[pt] : 0.0;
+            }
+        }
+        // ---- the singular pair itself (u, v = x / |x|), element-major so that a warp's
+        //      32 points write 32 consecutive values of each row
+        if (p.u_out && have) {
+            for (int i = 0; i < n; ++i) {
+                const double2 u = ok ? FLD(i, FY) : make_double2(0.0, 0.0);
+                const double2 xv = ok ? FLD(i, FX) : make_double2(0.0, 0.0);
+                p.u_out[(int64_t)i * p.npts + pt] = u;
+                p.v_out[(int64_t)i * p.npts + pt] = make_double2(xv.x * inv_nx, xv.y * inv_nx);
             }
         }
 

@@ -88,6 +88,7 @@ struct KParams {
     const double *gweight;
     double2 *grad_z;
     double2 *grad_bands;
+    double2 *u_out, *v_out;  // gradient kernel: the singular pair, u_out[i * npts + pt] (or null)
     // outputs (flat grid index; point index for the gradient kernel)
     double *sigma;
     uint32_t *mask;

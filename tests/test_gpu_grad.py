@@ -172,3 +172,47 @@ def test_newton_refinement_lands_on_the_contour():
     assert np.all(ref.x <= grid.re_min + (ref.col + 1) * hx + 1e-12)
     s_or, _, _ = oracle.sigma_min_banded(b, kl, ku, ref.x[:12] + 1j * ref.y[:12])
     assert np.all(np.abs(s_or - eps) <= 1e-9 * eps)
+
+
+def test_singular_pairs_and_band_gradient_from_them():
+    """psa_sigma_min_pairs writes a singular pair (B v = sigma u, unit vectors, the phases
+    of grad_z = conj(u^* v)); the band gradient contracted from stored pairs equals the
+    adjoint kernel's weighted band gradient; a reusable workspace gives the same bits."""
+    b, kl, ku, _ = inputs.random_toeplitz(70, 2, 4, seed=6)
+    A = oracle.band_to_dense(b, kl, ku)
+    rng = np.random.default_rng(8)
+    z = rng.uniform(-12, 12, 40) + 1j * rng.uniform(-12, 12, 40)
+    w = rng.standard_normal(40)
+    bt, zt, wt = _t(b), _t(z), _t(w, torch.float64)
+    ws = psa.GradWorkspace(70, kl, ku, 64, TIGHT, device=DEV)
+    r = psa.sigma_min_grad(bt, kl, ku, zt, opts=TIGHT, pairs=True, workspace=ws)
+    g1 = psa.sigma_min_grad(bt, kl, ku, zt, weight=wt, opts=TIGHT, workspace=ws)
+    g2 = psa.sigma_min_grad(bt, kl, ku, zt, weight=wt, opts=TIGHT)
+    gb = psa.band_grad_from_pairs(70, kl, ku, r.u, r.v, wt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g1.sigma.cpu().numpy(), g2.sigma.cpu().numpy())
+    np.testing.assert_array_equal(r.sigma.cpu().numpy(), g1.sigma.cpu().numpy())
+    u, v, s = r.u.cpu().numpy(), r.v.cpu().numpy(), r.sigma.cpu().numpy()
+    for p in range(40):
+        B = z[p] * np.eye(70) - A
+        assert abs(np.linalg.norm(u[:, p]) - 1) < 1e-12 and abs(np.linalg.norm(v[:, p]) - 1) < 1e-12
+        assert np.linalg.norm(B @ v[:, p] - s[p] * u[:, p]) <= 1e-9 * np.abs(B).sum(0).max()
+        assert abs(np.conj(np.vdot(u[:, p], v[:, p])) - r.grad_z.cpu().numpy()[p]) <= 1e-12
+    ref = g1.grad_bands.cpu().numpy()
+    np.testing.assert_allclose(gb.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_autograd_falls_back_to_the_adjoint_kernel_without_room_for_pairs(monkeypatch):
+    b, kl, ku, _ = inputs.random_toeplitz(50, 1, 3, seed=4)
+    rng = np.random.default_rng(5)
+    z = rng.uniform(-6, 6, 10) + 1j * rng.uniform(-6, 6, 10)
+    w = rng.standard_normal(10)
+    grads = []
+    for budget in (psa.PAIR_BUDGET, 0):
+        monkeypatch.setattr(psa, "PAIR_BUDGET", budget)
+        bt = _t(b).requires_grad_(True)
+        zt = _t(z).requires_grad_(True)
+        (psa.sigma_min_autograd(bt, zt, kl, ku, TIGHT) * _t(w, torch.float64)).sum().backward()
+        grads.append((bt.grad.cpu().numpy(), zt.grad.cpu().numpy()))
+    np.testing.assert_array_equal(grads[0][1], grads[1][1])
+    np.testing.assert_allclose(grads[0][0], grads[1][0], rtol=0, atol=1e-12 * np.abs(grads[1][0]).max())
