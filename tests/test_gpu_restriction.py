@@ -8,6 +8,8 @@ import torch
 
 import paper_2605_04550_gb300 as psa
 from paper_2605_04550_gb300 import _native, inputs, mlp, restriction
+import oracle
+from oracle import features as FO
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -27,30 +29,21 @@ def _dense(b, kl, ku):
     return A
 
 
-def test_matrix_stats_match_numpy():
+def test_matrix_stats_match_the_feature_oracle():
     b, kl, ku, a = inputs.random_toeplitz(150, 2, 5, seed=11)
     b = b + 0.01 * np.random.default_rng(0).standard_normal(b.shape)
     b = inputs._zero_outside(b.astype(np.complex128), 150, kl, ku)
     ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
     st = ctx.stats.cpu().numpy()
-    A = _dense(b, kl, ku)
-    fro = np.linalg.norm(A)
-    assert np.isclose(st[0], np.trace(A).real / 150, rtol=1e-12)
-    assert np.isclose(st[1], np.trace(A).imag / 150, rtol=1e-12, atol=1e-14)
-    assert np.isclose(st[3], fro, rtol=1e-12)
-    assert np.isclose(st[4], np.abs(A).sum(0).max(), rtol=1e-12)
-    assert np.isclose(st[5], np.abs(A).sum(1).max(), rtol=1e-12)
-    assert np.isclose(st[6], np.linalg.norm(A - A.T), rtol=1e-10)
-    assert np.isclose(st[7], np.linalg.norm(A - A.conj().T), rtol=1e-10)
-    d = np.abs(np.diag(A))
-    assert np.isclose(st[8], d.mean(), rtol=1e-12) and np.isclose(st[9], d.std(), rtol=1e-8)
-    # symbol of the diagonal means
-    abar = np.array([np.mean(np.diag(A, dd)) for dd in range(-kl, ku + 1)])
-    t = 2 * np.pi * np.arange(256) / 256
-    f = (abar[None, :] * np.exp(1j * np.outer(t, np.arange(-kl, ku + 1)))).sum(1)
+    ref, f = FO.matrix_stats(b, kl, ku)
+    np.testing.assert_allclose(st, ref, rtol=1e-10, atol=1e-13 * np.abs(ref).max())
     np.testing.assert_allclose(ctx.symbol.cpu().numpy(), f, rtol=0, atol=1e-12 * np.abs(f).max())
-    cen = np.trace(A) / 150
-    assert np.isclose(st[2], np.abs(f - cen).max(), rtol=1e-12)
+    # global features from the library's statistics and the oracle's sigma_min probes
+    cen = complex(ref[0], ref[1])
+    s4, _, _ = oracle.sigma_min_banded(b, kl, ku, np.array([0.0, cen + 0.5, cen + 1.0, cen + 2.0]),
+                                       k_max=300, tol=1e-6)
+    g = ctx.glob.cpu().numpy()
+    np.testing.assert_allclose(g, FO.global_features(ref, s4, restriction.EPS), rtol=2e-5, atol=2e-5)
 
 
 def test_resolvent_probe_features_closed_form():
@@ -74,7 +67,7 @@ def test_resolvent_probe_features_closed_form():
         assert abs(g[20 + k] - np.log10(st[2] / sk)) < 2e-5
 
 
-def test_point_features_match_numpy():
+def test_point_features_match_the_feature_oracle():
     b, kl, ku = inputs.grcar(120)
     ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
     grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 23, 17)
@@ -84,37 +77,12 @@ def test_point_features_match_numpy():
     np.testing.assert_array_equal(xi, x[[5, 77, 390]])
     st = ctx.stats.cpu().numpy()
     sym = ctx.symbol.cpu().numpy()
-    cen = st[0] + 1j * st[1]
-    R = st[2]
-    xs = grid.re_min + np.arange(grid.nx) * (4.0 / 22)
-    ys = grid.im_min + np.arange(grid.ny) * (7.0 / 16)
-    for f in (0, 5, 77, 200, 390):
-        i, j = divmod(f, grid.nx)
-        z = xs[j] + 1j * ys[i]
-        cx, cy = (xs[j] - 1.0) / 2.0, ys[i] / 3.5
-        ref = [cx, cy]
-        for k in range(1, 7):
-            w = 2 ** k
-            ref += [np.sin(w * cx), np.sin(w * cy), np.cos(w * cx), np.cos(w * cy)]
-        d = np.abs(sym - z)
-        ang = np.angle(np.roll(sym - z, -1) / (sym - z)).sum()
-        # distance to the closed polyline through the samples: the nearest point of each
-        # piece s_{k-1} -> s_k
-        s0, s1 = np.roll(sym, 1), sym
-        e = s1 - s0
-        t = np.clip(np.real(np.conj(e) * (z - s0)) / np.maximum(np.abs(e) ** 2, 1e-300), 0.0, 1.0)
-        dpoly = np.abs(s0 + t * e - z).min()
-        assert dpoly <= d.min()
-        ref += [dpoly / R, abs(z - cen) / R, d.mean() / R, np.log10(dpoly / R + 1e-7),
-                np.log10(d.mean() / R + 1e-7), np.rint(ang / (2 * np.pi))]
-        # BF16 rows: 8 significant bits
-        np.testing.assert_allclose(x[f, :32], np.array(ref), rtol=1e-2, atol=2e-2)
-        gl = ctx.glob.cpu().numpy()
-        np.testing.assert_allclose(x[f, 32:32 + _native.GLOBAL_FEATURES], gl, rtol=1e-2, atol=1e-3)
-        # log10(distance / eps), with gl[24] = log10(eps / R)
-        np.testing.assert_allclose(x[f, 32 + _native.GLOBAL_FEATURES], np.log10(dpoly / R + 1e-7) - gl[24],
-                                   rtol=1e-2, atol=2e-2)
-        assert np.all(x[f, 33 + _native.GLOBAL_FEATURES:] == 0)
+    gl = ctx.glob.cpu().numpy().astype(np.float64)
+    pts = np.arange(grid.npoints)
+    ref = FO.point_features(grid, st, sym, gl, pts)
+    # BF16 rows: 8 significant bits
+    np.testing.assert_allclose(x, ref, rtol=1e-2, atol=2e-2)
+    assert np.all(x[:, 33 + _native.GLOBAL_FEATURES:] == 0)
 
 
 def test_region_and_tile_list_match_numpy():
