@@ -49,10 +49,10 @@ WORKLOAD = (f"random banded Toeplitz n={N} kl={KL} ku={KU} (complex N(0,1) coeff
 # nominal FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per Lanczos row-step of k_sigma_min<2,5>: ncu's
-# dram__bytes_read.sum + dram__bytes_write.sum of one main-pass launch of the reduced
-# case (--case small: n = 256, 384 x 384 grid, 198.9 GB for 3.70e8 row-steps). Factor
+# dram__bytes_read.sum + dram__bytes_write.sum of one main-pass launch of this workload
+# itself (--case grid2000, application replay: 9.99 TB for 1.83e10 row-steps). Factor
 # rows and Lanczos vectors are streamed once per sweep, so traffic scales with row-steps.
-DRAM_BYTES_PER_ROW_STEP = 537.0
+DRAM_BYTES_PER_ROW_STEP = 546.0
 
 
 # the classifiers trained by `bench.py --workload restriction --save-model ...`
@@ -68,7 +68,7 @@ def workload(case: str = "mid"):
     if case == "grcar100":  # the first workload: Grcar n = 100 on its 100 x 100 grid
         bands, kl, ku = inputs.grcar(100)
         return bands, kl, ku, inputs.grcar_grid_100()
-    n, nx, ny = (N, NX, NY) if case == "mid" else (SMALL["n"], SMALL["nx"], SMALL["ny"])
+    n, nx, ny = (N, NX, NY) if case in ("mid", "grid2000") else (SMALL["n"], SMALL["nx"], SMALL["ny"])
     bands, kl, ku, a = inputs.random_toeplitz(n, KL, KU, seed=SEED)
     grid = inputs.toeplitz_symbol_grid(a, kl, ku, nx, ny)
     return bands, kl, ku, grid
@@ -498,8 +498,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": DRAM_BYTES_PER_ROW_STEP * float(steps.sum()) * n,
-                     "traffic_source": "ncu dram bytes per Lanczos row-step of one main-pass launch of the n=256 "
-                                       "case (bench.py --case small), scaled by this launch's row-steps",
+                     "traffic_source": "ncu dram bytes per Lanczos row-step of one main-pass launch of this "
+                                       "workload (bench.py --case grid2000), scaled by this launch's row-steps",
                      "peak_source": "FP64 from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                      "peak_probe_tflops": 2 * probe / 1e12,
                      "frac_of_probe": achieved / (2 * probe / 1e12),
@@ -937,9 +937,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100"],
+    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100", "grid2000"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures; "
-                         "grcar100: the Grcar n = 100 workload (small-order profile)")
+                         "grcar100: the Grcar n = 100 workload (small-order profile); grid2000: the "
+                         "benchmark workload's grid timing alone (full-size profiles)")
     ap.add_argument("--workload", default="grid",
                     choices=["grid", "differentiation", "batched", "restriction", "classifier"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "

@@ -224,6 +224,28 @@ int psa_sigma_min_pairs(const psa_band *A, const psa_c64 *z, int64_t n_pts, doub
 int psa_band_grad_from_pairs(const psa_band *A, int64_t n_pts, const psa_c64 *u, const psa_c64 *v,
                              const double *weight, psa_c64 *grad_bands, void *stream);
 
+/* Newton refinement of eps-contour crossings along grid rows (the level set
+ * sigma_min(zI - A) = eps of paper Sec. 2, Definition "Pseudospectrum", on the
+ * grid lines of Sec. 2.1). A crossing c of row rows[c] lies between columns
+ * cols[c] and cols[c] + 1, where sigma - eps changes sign (s_lo, s_hi: sigma at
+ * the two grid points). psa_contour_init sets the bracket lo, hi, the ordinate
+ * y, the sign of f = sigma - eps at the left end (flo_neg), the first iterate x
+ * (log sigma interpolated between the ends, kept within [0.05, 0.95] of the
+ * bracket) and z = x + i y; done = 0, resid = inf. psa_contour_step takes sigma
+ * and grad_z of psa_sigma_min_grad at z for the running crossings idx[0 .. na)
+ * (sigma[a], grad_z[a] belong to crossing idx[a]) and, per crossing: resid =
+ * |f| / eps, done when resid <= rtol or the bracket is narrower than 4 ulp;
+ * the bracket end whose sign f has moves to x; the next x is the Newton step
+ * x - f / (d sigma / d Re z) if it stays inside the bracket, else the
+ * bracket's midpoint; z is updated. All arrays DEVICE, m (or na) entries;
+ * asynchronous on stream. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_contour_init(int32_t m, const int32_t *rows, const int32_t *cols, const psa_grid *g, const double *s_lo,
+                     const double *s_hi, double eps, double *x, double *lo, double *hi, double *y, uint8_t *flo_neg,
+                     uint8_t *done, double *resid, psa_c64 *z, void *stream);
+int psa_contour_step(int32_t na, const int32_t *idx, const double *sigma, const psa_c64 *grad_z, double eps,
+                     double rtol, double *x, double *lo, double *hi, const double *y, const uint8_t *flo_neg,
+                     uint8_t *done, double *resid, psa_c64 *z, void *stream);
+
 /* Size of the fixed device scratch used by psa_sigma_min_static (64 MiB). */
 #define PSA_STATIC_SCRATCH_BYTES (64u << 20)
 

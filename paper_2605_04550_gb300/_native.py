@@ -30,6 +30,8 @@ EXPORTS = (
     "psa_sigma_min_grad",
     "psa_sigma_min_pairs",
     "psa_band_grad_from_pairs",
+    "psa_contour_init",
+    "psa_contour_step",
     "psa_batch_plan_bytes",
     "psa_batch_plan",
     "psa_batch_workspace_bytes",
@@ -130,6 +132,10 @@ def load(path: str | None = None):
                                             ctypes.POINTER(PsaLanczosOpts), vp, ctypes.c_size_t, vp]
         lib.psa_band_grad_from_pairs.restype = ctypes.c_int
         lib.psa_band_grad_from_pairs.argtypes = [ctypes.POINTER(PsaBand), i64, vp, vp, vp, vp, vp]
+        lib.psa_contour_init.restype = ctypes.c_int
+        lib.psa_contour_init.argtypes = [i32, vp, vp, ctypes.POINTER(PsaGrid), vp, vp, dbl] + [vp] * 8 + [vp]
+        lib.psa_contour_step.restype = ctypes.c_int
+        lib.psa_contour_step.argtypes = [i32, vp, vp, vp, dbl, dbl] + [vp] * 8 + [vp]
         lib.psa_batch_plan_bytes.restype = ctypes.c_int
         lib.psa_batch_plan_bytes.argtypes = [i32, ctypes.POINTER(ctypes.c_size_t)]
         lib.psa_batch_plan.restype = ctypes.c_int

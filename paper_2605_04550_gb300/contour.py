@@ -10,8 +10,10 @@ f'(x) = d sigma / d Re z from the adjoint kernel, kept inside the bracket
 wrong direction, is replaced by bisection).
 
 All evaluations of one Newton iteration go to the GPU in one call of
-``sigma_min_grad``; the host only keeps the brackets (plain arithmetic on a few
-thousand numbers).
+``sigma_min_grad``, and the iteration's arithmetic (first iterate, bracket update,
+Newton or bisection step) runs in the library's psa_contour_init / psa_contour_step
+kernels; the host finds the crossings on the grid, selects the running ones and
+launches.
 """
 from __future__ import annotations
 
@@ -45,51 +47,43 @@ def grid_crossings(sigma: np.ndarray, eps: float):
 def refine_rows(bands, kl: int, ku: int, grid: Grid, sigma: np.ndarray, eps: float,
                 max_iter: int = 40, rtol: float = 1e-12, opts: Optional[LanczosOpts] = None) -> ContourRefinement:
     """Refine every row crossing of the eps-contour of a computed grid field `sigma` (ny, nx)."""
-    import torch
+    import ctypes
 
+    import torch
+    from . import _native
+
+    lib = _native.load()
     rows, cols = grid_crossings(sigma, eps)
-    hx = (grid.re_max - grid.re_min) / (grid.nx - 1)
-    hy = (grid.im_max - grid.im_min) / max(grid.ny - 1, 1)
-    lo = grid.re_min + cols * hx
-    hi = grid.re_min + (cols + 1) * hx
-    y = grid.im_min + rows * hy
-    s_lo = np.asarray(sigma)[rows, cols]
-    s_hi = np.asarray(sigma)[rows, cols + 1]
-    # start from the interpolation of log(sigma) between the bracket ends
-    with np.errstate(divide="ignore", invalid="ignore"):
-        t = (np.log(eps) - np.log(np.maximum(s_lo, 1e-300))) / (np.log(np.maximum(s_hi, 1e-300)) -
-                                                                np.log(np.maximum(s_lo, 1e-300)))
-    t = np.where(np.isfinite(t), np.clip(t, 0.05, 0.95), 0.5)
-    x = lo + t * (hi - lo)
-    f_lo_neg = s_lo <= eps          # sign of f = sigma - eps at the left end (<= 0 there)
-    m = x.size
-    done = np.zeros(m, dtype=bool)
-    resid = np.full(m, np.inf)
-    it = 0
-    o = opts or LanczosOpts(tol=1e-15, k_max=4000)
+    m = int(rows.size)
     dev = bands.device
+    s_np = np.asarray(sigma)
+    t32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32), device=dev)
+    t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    r_t, c_t = t32(rows), t32(cols)
+    s_lo, s_hi = t64(s_np[rows, cols]), t64(s_np[rows, cols + 1])
+    x, lo, hi, y, resid = (torch.empty(max(m, 1), dtype=torch.float64, device=dev) for _ in range(5))
+    flo_neg, done = (torch.empty(max(m, 1), dtype=torch.uint8, device=dev) for _ in range(2))
+    z = torch.empty(max(m, 1), dtype=torch.complex128, device=dev)
+    g = _native.PsaGrid(float(grid.re_min), float(grid.re_max), float(grid.im_min), float(grid.im_max),
+                        int(grid.nx), int(grid.ny))
+    st = torch.cuda.current_stream(dev).cuda_stream
+    _native.check(lib.psa_contour_init(m, r_t.data_ptr(), c_t.data_ptr(), ctypes.byref(g), s_lo.data_ptr(),
+                                       s_hi.data_ptr(), float(eps), x.data_ptr(), lo.data_ptr(), hi.data_ptr(),
+                                       y.data_ptr(), flo_neg.data_ptr(), done.data_ptr(), resid.data_ptr(),
+                                       z.data_ptr(), st), "psa_contour_init")
+    o = opts or LanczosOpts(tol=1e-15, k_max=4000)
+    it = 0
     for it in range(1, max_iter + 1):
-        act = np.flatnonzero(~done)
-        if act.size == 0:
+        act = torch.nonzero(done[:m] == 0).reshape(-1).to(torch.int32)
+        if act.numel() == 0:
             it -= 1
             break
-        z = torch.as_tensor(x[act] + 1j * y[act], dtype=torch.complex128, device=dev)
-        r = sigma_min_grad(bands, kl, ku, z, opts=o)
-        s = r.sigma.cpu().numpy()
-        g = r.grad_z.cpu().numpy().real          # d sigma / d Re z
-        f = s - eps
-        resid[act] = np.abs(f) / eps
-        conv = resid[act] <= rtol
-        done[act[conv]] = True
-        # shrink the brackets: the left end keeps the sign it had on the grid
-        same_as_lo = (f <= 0) == f_lo_neg[act]
-        lo[act] = np.where(same_as_lo, x[act], lo[act])
-        hi[act] = np.where(same_as_lo, hi[act], x[act])
-        with np.errstate(divide="ignore", invalid="ignore"):
-            xn = x[act] - f / g
-        ok = np.isfinite(xn) & (xn > lo[act]) & (xn < hi[act])
-        xn = np.where(ok, xn, 0.5 * (lo[act] + hi[act]))
-        width = hi[act] - lo[act]
-        done[act[width <= 4e-16 * np.maximum(np.abs(lo[act]), 1.0)]] = True
-        x[act] = np.where(conv, x[act], xn)
-    return ContourRefinement(x=x, y=y, row=rows, col=cols, residual=resid, iterations=it, converged=done & (resid <= rtol))
+        r = sigma_min_grad(bands, kl, ku, z.index_select(0, act.long()), opts=o)
+        _native.check(lib.psa_contour_step(int(act.numel()), act.data_ptr(), r.sigma.data_ptr(),
+                                           r.grad_z.data_ptr(), float(eps), float(rtol), x.data_ptr(),
+                                           lo.data_ptr(), hi.data_ptr(), y.data_ptr(), flo_neg.data_ptr(),
+                                           done.data_ptr(), resid.data_ptr(), z.data_ptr(), st),
+                      "psa_contour_step")
+    res = resid[:m].cpu().numpy()
+    return ContourRefinement(x=x[:m].cpu().numpy(), y=y[:m].cpu().numpy(), row=rows, col=cols, residual=res,
+                             iterations=it, converged=(done[:m].cpu().numpy() != 0) & (res <= rtol))

@@ -216,3 +216,65 @@ def test_autograd_falls_back_to_the_adjoint_kernel_without_room_for_pairs(monkey
         grads.append((bt.grad.cpu().numpy(), zt.grad.cpu().numpy()))
     np.testing.assert_array_equal(grads[0][1], grads[1][1])
     np.testing.assert_allclose(grads[0][0], grads[1][0], rtol=0, atol=1e-12 * np.abs(grads[1][0]).max())
+
+
+def test_contour_kernels_match_the_bracketed_newton_rule():
+    """psa_contour_init / psa_contour_step against the rule written out in NumPy: the
+    first iterate interpolates log sigma within [0.05, 0.95] of the bracket; a step keeps
+    the end whose sign f has, takes the Newton step when it stays inside, else bisects."""
+    import ctypes
+    from paper_2605_04550_gb300 import _native
+    lib = _native.load()
+    rng = np.random.default_rng(3)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 50, 40)
+    m = 300
+    rows = rng.integers(0, grid.ny, m).astype(np.int32)
+    cols = rng.integers(0, grid.nx - 1, m).astype(np.int32)
+    eps = 1e-4
+    s_lo = 10.0 ** rng.uniform(-6, -2, m)
+    s_hi = np.where(s_lo <= eps, 10.0 ** rng.uniform(-4, -2, m), 10.0 ** rng.uniform(-7, -4, m))
+    s_lo[:5] = 0.0  # log of zero: the midpoint
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+    x, lo, hi, y, resid = (torch.empty(m, dtype=torch.float64, device=DEV) for _ in range(5))
+    flo, done = (torch.empty(m, dtype=torch.uint8, device=DEV) for _ in range(2))
+    z = torch.empty(m, dtype=torch.complex128, device=DEV)
+    g = _native.PsaGrid(grid.re_min, grid.re_max, grid.im_min, grid.im_max, grid.nx, grid.ny)
+    ptrs = [t.data_ptr() for t in (x, lo, hi, y, flo, done, resid, z)]
+    r_t, c_t, sl_t, sh_t = T(rows, torch.int32), T(cols, torch.int32), T(s_lo), T(s_hi)
+    assert lib.psa_contour_init(m, r_t.data_ptr(), c_t.data_ptr(), ctypes.byref(g), sl_t.data_ptr(),
+                                sh_t.data_ptr(), eps, *ptrs, None) == 0
+    hx, hy = 4.0 / 49, 7.0 / 39
+    a, b = grid.re_min + cols * hx, grid.re_min + (cols + 1) * hx
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = (np.log(eps) - np.log(np.maximum(s_lo, 1e-300))) / (np.log(np.maximum(s_hi, 1e-300)) -
+                                                                np.log(np.maximum(s_lo, 1e-300)))
+    t = np.where(np.isfinite(t), np.clip(t, 0.05, 0.95), 0.5)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(lo.cpu().numpy(), a, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(y.cpu().numpy(), grid.im_min + rows * hy, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(x.cpu().numpy(), a + t * (b - a), rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(flo.cpu().numpy(), (s_lo <= eps).astype(np.uint8))
+    # one step for every other crossing
+    act = np.arange(0, m, 2, dtype=np.int32)
+    x0, lo0, hi0 = x.cpu().numpy(), lo.cpu().numpy(), hi.cpu().numpy()
+    sig = eps * (1 + rng.uniform(-0.5, 0.5, act.size))
+    sig[:3] = eps * (1 + 1e-14)  # converged
+    slope = rng.uniform(-2e-3, 2e-3, act.size) + 1j * rng.standard_normal(act.size)
+    a_t, s_t, g_t = T(act, torch.int32), T(sig), T(slope, torch.complex128)
+    assert lib.psa_contour_step(act.size, a_t.data_ptr(), s_t.data_ptr(), g_t.data_ptr(), eps, 1e-12,
+                                *ptrs, None) == 0
+    torch.cuda.synchronize()
+    f = sig - eps
+    same = (f <= 0) == (s_lo[act] <= eps)
+    l = np.where(same, x0[act], lo0[act])
+    h = np.where(same, hi0[act], x0[act])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xn = x0[act] - f / slope.real
+    xn = np.where(np.isfinite(xn) & (xn > l) & (xn < h), xn, 0.5 * (l + h))
+    conv = np.abs(f) / eps <= 1e-12
+    np.testing.assert_array_equal(lo.cpu().numpy()[act], l)
+    np.testing.assert_array_equal(hi.cpu().numpy()[act], h)
+    np.testing.assert_array_equal(x.cpu().numpy()[act], np.where(conv, x0[act], xn))
+    np.testing.assert_array_equal(done.cpu().numpy()[act], (conv | (h - l <= 4e-16 * np.maximum(np.abs(l), 1))))
+    np.testing.assert_array_equal(x.cpu().numpy()[1::2], x0[1::2])  # crossings not in the list keep their state
+    np.testing.assert_array_equal(z.cpu().numpy()[act].real, x.cpu().numpy()[act])
