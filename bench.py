@@ -896,6 +896,22 @@ def run_classifier(args):
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1) / args.steps
     fwd_flops = 2.0 * rows * (mlp.IN * mlp.HIDDEN + 2 * mlp.HIDDEN * mlp.HIDDEN + mlp.HIDDEN)
+    # the paper's dual-path network on the same rows: its fused, padded GEMMs (128 -> 256,
+    # 256 -> 128, three 128 -> 128) as the tensor cores run them
+    theta_d = mlp.init_theta(0, dev, "dual")
+    nbd = mlp.workspace_bytes(rows, False, "dual")
+    bufd, ptrd = mlp._aligned_buffer(nbd, dev)
+    for _ in range(args.warmup):
+        mlp.forward(theta_d, x, out=prob, workspace=(bufd, ptrd, nbd), net="dual")
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        mlp.forward(theta_d, x, out=prob, workspace=(bufd, ptrd, nbd), net="dual")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    dual_ms = e0.elapsed_time(e1) / args.steps
+    dual_flops = 2.0 * rows * (256 * 128 + 128 * 256 + 3 * 128 * 128 + 128)
+    del bufd
     M = N = K = 8192
     A = (torch.randn(M, K, device=dev, generator=g)).to(torch.bfloat16)
     B = (torch.randn(N, K, device=dev, generator=g)).to(torch.bfloat16)
@@ -919,6 +935,9 @@ def run_classifier(args):
             "roofline": {"bound": "tensor", "achieved": fwd_flops / (fwd_ms * 1e-3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms * 1e-3) / 1e12 / peak, "traffic": None,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"},
+            "dual_path": {"ms": dual_ms, "rows_per_s": rows / (dual_ms * 1e-3),
+                          "tflops_padded": dual_flops / (dual_ms * 1e-3) / 1e12,
+                          "trainable_parameters": mlp._native.DUAL_TRAINABLE},
             "gemm_8192": {"ms": gemm_ms, "tflops": gemm_tf, "frac_of_bf16_peak": gemm_tf / peak,
                           "max_rel_err_vs_fp32": err}}
     print(json.dumps(line), flush=True)

@@ -74,11 +74,15 @@ def refine_rows(bands, kl: int, ku: int, grid: Grid, sigma: np.ndarray, eps: flo
     o = opts or LanczosOpts(tol=1e-15, k_max=4000)
     it = 0
     for it in range(1, max_iter + 1):
-        act = torch.nonzero(done[:m] == 0).reshape(-1).to(torch.int32)
-        if act.numel() == 0:
+        # the running crossings and their iterates, selected on the host (a few thousand
+        # values; copies only, so no other kernels run on the device)
+        act_h = np.flatnonzero(done[:m].cpu().numpy() == 0).astype(np.int32)
+        if act_h.size == 0:
             it -= 1
             break
-        r = sigma_min_grad(bands, kl, ku, z.index_select(0, act.long()), opts=o)
+        act = torch.as_tensor(act_h, device=dev)
+        z_act = torch.as_tensor(z[:m].cpu().numpy()[act_h], device=dev)
+        r = sigma_min_grad(bands, kl, ku, z_act, opts=o)
         _native.check(lib.psa_contour_step(int(act.numel()), act.data_ptr(), r.sigma.data_ptr(),
                                            r.grad_z.data_ptr(), float(eps), float(rtol), x.data_ptr(),
                                            lo.data_ptr(), hi.data_ptr(), y.data_ptr(), flo_neg.data_ptr(),
