@@ -317,3 +317,20 @@ def test_single_call_graph_capture_replays_bitwise():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.sigma.cpu().numpy(), ref2.sigma.cpu().numpy())
     assert not np.array_equal(ref2.sigma.cpu().numpy(), ref.sigma.cpu().numpy())
+
+
+def test_default_workspace_is_reused_between_calls():
+    """Without workspace=, sigma_min keeps its last workspace per device: a second call of
+    the same shape allocates nothing and gives the same bits; release_workspaces frees it."""
+    bands, kl, ku = inputs.grcar(100)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 40, 30)
+    b = torch.as_tensor(bands, device=DEV)
+    psa.release_workspaces()
+    o1 = psa.sigma_min(b, kl, ku, grid)
+    ws1 = psa._default_ws[str(b.device)][1]
+    o2 = psa.sigma_min(b, kl, ku, grid)
+    assert psa._default_ws[str(b.device)][1] is ws1
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(o1.sigma.cpu().numpy(), o2.sigma.cpu().numpy())
+    psa.release_workspaces()
+    assert not psa._default_ws
