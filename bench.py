@@ -859,6 +859,136 @@ def run_restriction(args):
     return 0
 
 
+def _banded_eigvals(item):
+    """Eigenvalues of a band (LAPACK zgeev through numpy on the dense matrix): the
+    paper's own input to its spectrum features. Runs in a worker process."""
+    b, kl, ku = item
+    n = b.shape[1]
+    A = np.zeros((n, n), dtype=np.complex128)
+    for d in range(-kl, ku + 1):
+        i = np.arange(max(0, -d), min(n, n - d))
+        A[i, i + d] = b[d + kl, i]
+    t0 = time.perf_counter()
+    lam = np.linalg.eigvals(A)
+    return lam, time.perf_counter() - t0
+
+
+def _eigvals_pool(items, workers: int):
+    """Eigenvalues of many bands on single-threaded worker processes (spawned)."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(_banded_eigvals, items, chunksize=1)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [o[0] for o in out], float(sum(o[1] for o in out))
+
+
+def run_feature_ablation(args):
+    """The paper's eigenvalue features (Sec. 3.1, Tables "matrix" and "matrixAdd"; Eq.
+    (dist) over the eigenvalues) against the symbol-curve features that the library
+    uses by default: the same network, labels, sampled points, training batches and
+    validation truth, at orders where a dense eigensolve is affordable (n log-uniform
+    in [300, 1500]); then recall and grid fraction on held-out test matrices and on
+    the benchmark matrix (n = 2000, 512 x 512) at each calibrated threshold."""
+    import torch
+    import paper_2605_04550_gb300 as psa
+    from paper_2605_04550_gb300 import inputs as inp, restriction
+    workers = max(1, min(os.cpu_count() or 1, 32))
+    n_min, n_max = 300, 1500
+    tr = inp.restriction_matrices(args.ablation_train, seed=1, n_min=n_min, n_max=n_max, nx=32, ny=32)
+    va = inp.restriction_matrices(args.restrict_val, seed=2, n_min=n_min, n_max=n_max, nx=args.restrict_val_grid,
+                                  ny=args.restrict_val_grid)
+    te = inp.restriction_matrices(args.restrict_val, seed=3, n_min=n_min, n_max=n_max, nx=args.restrict_val_grid,
+                                  ny=args.restrict_val_grid)
+    bb, bkl, bku, bgrid = workload("mid")
+    t0 = time.perf_counter()
+    lam_all, eig_cpu_s = _eigvals_pool([(b, kl, ku) for b, kl, ku, *_ in tr + va + te] + [(bb, bkl, bku)], workers)
+    eig_wall = time.perf_counter() - t0
+    lam_tr, lam_va = lam_all[:len(tr)], lam_all[len(tr):len(tr) + len(va)]
+    lam_te, lam_b = lam_all[len(tr) + len(va):-1], lam_all[-1]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    eps = restriction.EPS
+    opts_truth = psa.LanczosOpts(k_min=2, k_max=KMAX, tol=TOL)
+
+    def truth_of(mats, grids):
+        plan, sg = restriction.labels_batched(mats, grids, eps, opts=opts_truth)
+        sg = sg.cpu().numpy()
+        return [sg[o:o + g.npoints].reshape(g.ny, g.nx) for o, g in zip(plan.offsets, grids)]
+
+    t0 = time.perf_counter()
+    mats = [(torch.as_tensor(b, device=dev), kl, ku) for b, kl, ku, _, _ in tr]
+    grids = [g for *_, g, _ in tr]
+    vm = [(torch.as_tensor(b, device=dev), kl, ku) for b, kl, ku, _, _ in va]
+    vg = [g for *_, g, _ in va]
+    tm_ = [(torch.as_tensor(b, device=dev), kl, ku) for b, kl, ku, _, _ in te]
+    tg = [g for *_, g, _ in te]
+    vtruth, ttruth = truth_of(vm, vg), truth_of(tm_, tg)
+    bt = torch.as_tensor(bb, device=dev)
+    btruth = psa.sigma_min(bt, bkl, bku, bgrid, eps=(eps,), opts=opts_truth).sigma.cpu().numpy()
+    truth_s = time.perf_counter() - t0
+    nets = ["mlp", "dual"] if args.net == "both" else [args.net]
+    labels = None
+    result = {}
+    for feat in ("symbol", "eigen"):
+        sp = (lambda lst: lst) if feat == "eigen" else (lambda lst: None)
+        for net in nets:
+            m = restriction.Restriction(dev, seed=0, net=net, features=feat)
+            t0 = time.perf_counter()
+            x, y, _ = m.build_training_set(mats, grids, np.random.default_rng(0), spectra=sp(lam_tr), labels=labels)
+            labels = m.last_labels
+            m.train(x, y, np.random.default_rng(1))
+            torch.cuda.synchronize(dev)
+            train_s = time.perf_counter() - t0
+            del x, y
+            vctx = restriction.matrix_contexts(vm, eps, spectra=sp(lam_va))
+            cal = m.calibrate(vctx, vg, vtruth)
+            tctx = restriction.matrix_contexts(tm_, eps, spectra=sp(lam_te))
+            recs, fracs, precs = [], [], []
+            for c, g, s in zip(tctx, tg, ttruth):
+                p = m.predict(c, g)
+                r = restriction.region_mask(p.reshape(-1).contiguous(), g, m.tau).cpu().numpy().astype(bool)
+                met = restriction.recall_metrics(s <= eps, r)
+                recs.append(met["recall"])
+                fracs.append(met["grid_fraction"])
+                precs.append(met["precision"])
+            bctx = restriction.matrix_contexts([(bt, bkl, bku)], eps, spectra=sp([lam_b]))[0]
+            pb = m.predict(bctx, bgrid)
+            rb = restriction.region_mask(pb.reshape(-1).contiguous(), bgrid, m.tau).cpu().numpy().astype(bool)
+            result[f"{net}/{feat}"] = {
+                "tau": m.tau, "paper_rule_tau": cal["paper_rule_tau"],
+                "validation_min_recall": cal["row"]["min_recall"],
+                "validation_mean_grid_fraction": cal["row"]["mean_grid_fraction"],
+                "test_min_recall": float(np.min(recs)), "test_median_recall": float(np.median(recs)),
+                "test_p10_recall": float(np.percentile(recs, 10)),
+                "test_mean_grid_fraction": float(np.mean(fracs)), "test_mean_precision": float(np.mean(precs)),
+                "test_true_sensitive_fraction": float(np.mean([(s <= eps).mean() for s in ttruth])),
+                "bench_matrix": restriction.recall_metrics(btruth <= eps, rb),
+                "epochs": len(m.history), "final_val_loss": m.history[-1]["val_loss"], "train_s": train_s}
+    line = {"workload": "feature ablation: eigenvalue features (paper Sec. 3.1) vs symbol-curve features",
+            "config": {"training": f"{len(tr)} matrices, n log-uniform [{n_min}, {n_max}], 32x32 label grids "
+                                   f"(seed 1)",
+                       "validation": f"{len(va)} matrices (seed 2), {args.restrict_val_grid}^2 grids",
+                       "test": f"{len(te)} matrices (seed 3), {args.restrict_val_grid}^2 grids; and the benchmark "
+                               f"matrix (n={N}, kl={KL}, ku={KU}, {NX}x{NY})",
+                       "eps": eps, "truth": f"sigma_min to tol {TOL:g}",
+                       "same": "labels, sampled points, held-out split, batches, seeds, validation truth"},
+            "eigensolve": {"method": "numpy.linalg.eigvals (LAPACK zgeev) of the dense matrix, one thread per "
+                                     "matrix", "workers": workers, "cpu_s": eig_cpu_s, "wall_s": eig_wall,
+                           "matrices": len(lam_all)},
+            "truth_s": truth_s, "results": result}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def mlp_nparams(net: str) -> int:
     from paper_2605_04550_gb300 import _native
     return _native.MLP_PARAMS if net == "mlp" else _native.DUAL_TRAINABLE
@@ -961,12 +1091,14 @@ def main():
                          "grcar100: the Grcar n = 100 workload (small-order profile); grid2000: the "
                          "benchmark workload's grid timing alone (full-size profiles)")
     ap.add_argument("--workload", default="grid",
-                    choices=["grid", "differentiation", "batched", "restriction", "classifier"],
+                    choices=["grid", "differentiation", "batched", "restriction", "classifier", "features"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
-                         "batched: 256 matrices on their own grids; restriction: the learned restriction")
+                         "batched: 256 matrices on their own grids; restriction: the learned restriction; "
+                         "features: eigenvalue against symbol-curve features (ablation)")
     ap.add_argument("--batch-size", type=int, default=256, help="batched: number of matrices")
     ap.add_argument("--restrict-train", type=int, default=2000, help="restriction: training matrices")
     ap.add_argument("--restrict-val", type=int, default=30, help="restriction: validation matrices")
+    ap.add_argument("--ablation-train", type=int, default=600, help="features: training matrices")
     ap.add_argument("--restrict-val-grid", type=int, default=128, help="restriction: validation grid side")
     ap.add_argument("--restrict-test-n", type=int, default=20000, help="restriction: order of the test matrix")
     ap.add_argument("--restrict-grid", type=int, default=1024, help="restriction: test grid side")
@@ -991,6 +1123,8 @@ def main():
         return run_restriction(args)
     if args.workload == "classifier":
         return run_classifier(args)
+    if args.workload == "features":
+        return run_feature_ablation(args)
     return run_gpu(args)
 
 

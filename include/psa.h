@@ -523,6 +523,27 @@ int psa_global_features(const double *stats, const double *sigma4, double eps, f
 int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
                        const psa_c64 *symbol, const float *global, uint16_t *x, void *stream);
 
+/* The paper's own spectrum features (Sec. 3.1, Table "matrix", f1 .. f10)
+ * from a point set instead of the symbol curve: set[0 .. m) (DEVICE) is, for
+ * example, the eigenvalues of A computed by a dense eigensolver. Overwrites in
+ * stats (DEVICE, as written by psa_matrix_stats, whose centroid it keeps) the
+ * radius R = max |set - centroid| and the entries PSA_STAT_SYM_RE_MEAN ..
+ * PSA_STAT_SYM_RMIN with the mean, standard deviation, minimum and maximum of
+ * Re and Im of (set - centroid) and min |set - centroid|; call
+ * psa_global_features afterwards. Errors: PSA_EINVAL (m < 1, NULL), PSA_ECUDA. */
+int psa_point_set_stats(const psa_c64 *set, int32_t m, double *stats, void *stream);
+
+/* psa_point_features over any set of m >= 1 points (DEVICE set[0 .. m)).
+ * closed = 1: the set is a closed polyline set[0] -> .. -> set[m - 1] -> set[0]
+ * (psa_point_features is this with the PSA_SYMBOL_SAMPLES symbol samples);
+ * closed = 0: the set is a point set such as the eigenvalues, and g1 is the
+ * distance to its nearest point (Eq. (dist)), g3 the mean distance to its
+ * points and column 31 (the winding number) is 0. Distances are in units of
+ * stats' radius. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_point_features_set(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
+                           const psa_c64 *set, int32_t m, int32_t closed, const float *global, uint16_t *x,
+                           void *stream);
+
 /* Predicted region of the hybrid method (paper Sec. 3.6 and 4): mask[f] = 1
  * when some grid point within `radius` rows and columns of f (a box of
  * (2 radius + 1)^2 points, clipped to the grid) has prob >= tau. prob and

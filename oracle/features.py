@@ -6,8 +6,10 @@ shares no code with it. Each function writes the definition out directly, entry 
 entry, in FP64 (the library stores the point features in BF16).
 
 The features follow the paper's tables of matrix features and its per-point
-distances (Sec. 3.1, Tables "matrix", "matrixAdd" and "resolvent", Eq. (dist)),
-with the readings this library takes where the paper needs dense eigenvalues:
+distances (Sec. 3.1, Tables "matrix", "matrixAdd" and "resolvent", Eq. (dist)).
+With eigenvalues given (point_set_stats, point_features(closed=False)) they are
+the paper's own; by default they take the readings this library uses in place of
+dense eigenvalues:
 the eigenvalue set is replaced by the symbol curve of the diagonal means,
 f(t) = sum_d abar_d e^{i d t} at 256 points t_k = 2 pi k / 256, about the
 centroid trace(A) / n (the eigenvalue mean, Table 3); g1 is the distance to the
@@ -76,6 +78,19 @@ def matrix_stats(bands: np.ndarray, kl: int, ku: int):
     return st, f
 
 
+def point_set_stats(st: np.ndarray, pts) -> np.ndarray:
+    """The statistics with the spectrum entries taken over a point set (the paper's
+    eigenvalue features f1-f10, Sec. 3.1, Table "matrix"): about the centroid st[0:2],
+    R = max |p - c|, mean / std / min / max of Re and Im of (p - c), min |p - c|."""
+    out = np.array(st, dtype=np.float64)
+    x = np.asarray(pts, dtype=np.complex128).ravel() - complex(st[0], st[1])
+    out[2] = np.abs(x).max()
+    out[13], out[14], out[15], out[16] = x.real.mean(), x.real.std(), x.real.min(), x.real.max()
+    out[17], out[18], out[19], out[20] = x.imag.mean(), x.imag.std(), x.imag.min(), x.imag.max()
+    out[21] = np.abs(x).min()
+    return out
+
+
 def global_features(st: np.ndarray, sigma4, eps: float) -> np.ndarray:
     """28 scale-free global features. sigma4 = sigma_min(zI - A) at z = 0 and at the
     centroid + 0.5, + 1, + 2 (the resolvent norms of Table "resolvent" are their inverses)."""
@@ -127,13 +142,15 @@ def winding_number(f: np.ndarray, z: complex) -> int:
     return int(np.rint(ang / (2.0 * np.pi)))
 
 
-def point_features(grid, st: np.ndarray, f: np.ndarray, g: np.ndarray, flat_idx) -> np.ndarray:
+def point_features(grid, st: np.ndarray, f: np.ndarray, g: np.ndarray, flat_idx, closed: bool = True) -> np.ndarray:
     """Feature rows (FP64) of the flat grid indices: [0, 26) the Fourier encoding of Sec.
     3.2.1, [c, sin 2^k c, cos 2^k c] for k = 1..6 (sines and cosines of x and y
     interleaved as the library stores them) of the coordinates scaled to [-1, 1]^2;
     26..28 g1 (polyline), g2 (centroid), g3 (mean sample distance), in units of R;
     29, 30 log10 of g1 and g3; 31 the winding number; 32..59 the global features;
-    60 log10 of the polyline distance over eps; zeros after."""
+    60 log10 of the polyline distance over eps; zeros after.
+    closed=False: f is a point set (the eigenvalues, Eq. (dist)): g1 is the distance
+    to its nearest point, g3 the mean distance, column 31 is 0."""
     cen = st[0] + 1j * st[1]
     R = max(st[2], 1e-30)
     hx = (grid.re_max - grid.re_min) / (grid.nx - 1) if grid.nx > 1 else 0.0
@@ -151,10 +168,10 @@ def point_features(grid, st: np.ndarray, f: np.ndarray, g: np.ndarray, flat_idx)
             w = 2.0 ** k
             v[2 + 4 * (k - 1):6 + 4 * (k - 1)] = [np.sin(w * cx), np.sin(w * cy), np.cos(w * cx), np.cos(w * cy)]
         d = np.abs(f - z)
-        g1 = polyline_distance(f, z) / R
+        g1 = (polyline_distance(f, z) if closed else d.min()) / R
         v[26], v[27], v[28] = g1, abs(z - cen) / R, d.mean() / R
         v[29], v[30] = np.log10(g1 + 1e-7), np.log10(d.mean() / R + 1e-7)
-        v[31] = winding_number(f, z)
+        v[31] = winding_number(f, z) if closed else 0
         v[32:32 + GLOBAL] = g
         v[32 + GLOBAL] = v[29] - g[24]
         rows.append(v)

@@ -47,6 +47,8 @@ EXPORTS = (
     "psa_matrix_stats",
     "psa_global_features",
     "psa_point_features",
+    "psa_point_set_stats",
+    "psa_point_features_set",
     "psa_region",
     "psa_tile_slots",
     "psa_probe_dfma_rate",
@@ -170,6 +172,10 @@ def load(path: str | None = None):
         lib.psa_global_features.argtypes = [vp, vp, dbl, vp, vp]
         lib.psa_point_features.restype = ctypes.c_int
         lib.psa_point_features.argtypes = [ctypes.POINTER(PsaGrid), vp, i64, vp, vp, vp, vp, vp]
+        lib.psa_point_set_stats.restype = ctypes.c_int
+        lib.psa_point_set_stats.argtypes = [vp, i32, vp, vp]
+        lib.psa_point_features_set.restype = ctypes.c_int
+        lib.psa_point_features_set.argtypes = [ctypes.POINTER(PsaGrid), vp, i64, vp, vp, i32, i32, vp, vp, vp]
         lib.psa_region.restype = ctypes.c_int
         lib.psa_region.argtypes = [vp, ctypes.c_float, i32, i32, i32, vp, vp]
         lib.psa_tile_slots.restype = ctypes.c_int

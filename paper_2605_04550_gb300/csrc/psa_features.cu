@@ -234,25 +234,117 @@ __global__ void k_global_features(const double *st, const double *sigma4, double
     for (int k = 0; k < PSA_GLOBAL_FEATURES; ++k) g[k] = v[k];
 }
 
+// Spectrum statistics of a point set (the eigenvalues of A, for the paper's own
+// features f1 .. f10 of Sec. 3.1, Table "matrix") about the centroid already in
+// stats: they replace the symbol-sample statistics and the radius R.
+__global__ void __launch_bounds__(NT) k_point_set_stats(const double2 *pts, int m, double *stats)
+{
+    __shared__ double red[NT / 32];
+    const int tid = threadIdx.x;
+    const double cx = stats[PSA_STAT_CEN_RE], cy = stats[PSA_STAT_CEN_IM];
+    double sre = 0.0, sim = 0.0, sre2 = 0.0, sim2 = 0.0, rmaxs = 0.0;
+    double mnre = INFINITY, mxre = -INFINITY, mnim = INFINITY, mxim = -INFINITY, rmin = INFINITY;
+    for (int k = tid; k < m; k += NT) {
+        const double xr = pts[k].x - cx, xi = pts[k].y - cy, r = sqrt(xr * xr + xi * xi);
+        sre += xr;
+        sim += xi;
+        sre2 += xr * xr;
+        sim2 += xi * xi;
+        mnre = fmin(mnre, xr);
+        mxre = fmax(mxre, xr);
+        mnim = fmin(mnim, xi);
+        mxim = fmax(mxim, xi);
+        rmaxs = fmax(rmaxs, r);
+        rmin = fmin(rmin, r);
+    }
+    sre = block_sum(sre, red);
+    sim = block_sum(sim, red);
+    sre2 = block_sum(sre2, red);
+    sim2 = block_sum(sim2, red);
+    mnre = block_min(mnre, red);
+    mxre = block_max(mxre, red);
+    mnim = block_min(mnim, red);
+    mxim = block_max(mxim, red);
+    rmaxs = block_max(rmaxs, red);
+    rmin = block_min(rmin, red);
+    if (tid == 0) {
+        const double dm = (double)m;
+        stats[PSA_STAT_RADIUS] = rmaxs;
+        stats[PSA_STAT_SYM_RE_MEAN] = sre / dm;
+        stats[PSA_STAT_SYM_RE_STD] = sqrt(fmax(sre2 / dm - (sre / dm) * (sre / dm), 0.0));
+        stats[PSA_STAT_SYM_RE_MIN] = mnre;
+        stats[PSA_STAT_SYM_RE_MAX] = mxre;
+        stats[PSA_STAT_SYM_IM_MEAN] = sim / dm;
+        stats[PSA_STAT_SYM_IM_STD] = sqrt(fmax(sim2 / dm - (sim / dm) * (sim / dm), 0.0));
+        stats[PSA_STAT_SYM_IM_MIN] = mnim;
+        stats[PSA_STAT_SYM_IM_MAX] = mxim;
+        stats[PSA_STAT_SYM_RMIN] = rmin;
+    }
+}
+
+// points of the curve or set that one shared-memory pass holds
+constexpr int kSetChunk = 2048;
+
 // One feature row per point (flat grid index idx[p], or p on the full grid).
+// CLOSED: the set is the closed polyline through the symbol samples (distance to the
+// polyline, winding number); otherwise a point set such as the eigenvalues (distance
+// to the nearest point, no winding number). The set passes through shared memory in
+// chunks, each entry preceded by its predecessor on the closed curve.
+template <bool CLOSED>
 __global__ void k_point_features(double re_min, double im_min, double hx, double hy, int nx, int ny,
                                  const int32_t *idx, int64_t npts, const float *gfeat, const double *st,
-                                 const double2 *symbol, __nv_bfloat16 *x)
+                                 const double2 *set, int m, __nv_bfloat16 *x)
 {
-    __shared__ float2 sym[T];
+    __shared__ float2 sh[kSetChunk + 1];
     __shared__ float gf[PSA_GLOBAL_FEATURES];
     const double cr = st[PSA_STAT_CEN_RE], ci = st[PSA_STAT_CEN_IM];
     const float R = (float)fmax(st[PSA_STAT_RADIUS], 1e-30);
-    for (int k = threadIdx.x; k < T; k += blockDim.x)
-        sym[k] = make_float2((float)(symbol[k].x - cr), (float)(symbol[k].y - ci));
     for (int k = threadIdx.x; k < PSA_GLOBAL_FEATURES; k += blockDim.x) gf[k] = gfeat[k];
-    __syncthreads();
     const double xc = re_min + 0.5 * hx * (nx - 1), yc = im_min + 0.5 * hy * (ny - 1);
     const double hw = fmax(0.5 * hx * (nx - 1), 1e-300), hh = fmax(0.5 * hy * (ny - 1), 1e-300);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t f = idx ? (int64_t)idx[p] : p;
+    // every thread of a block takes the same number of passes (the chunk loads need all)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npts; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        const bool live = p < npts;
+        const int64_t f = live ? (idx ? (int64_t)idx[p] : p) : 0;
         const int i = (int)(f / nx), j = (int)(f - (int64_t)i * nx);
         const double zr = fma((double)j, hx, re_min), zi = fma((double)i, hy, im_min);
+        // distances (about the centroid, in units of R) and winding; for the closed
+        // curve dmin is the distance to the polyline through the samples (exact for a
+        // curve made of straight pieces, such as the segment of a kl = ku Grcar-type
+        // band, whose sensitive zone is a band of width about 2 eps around it)
+        const float pr = (float)(zr - cr), pi = (float)(zi - ci);
+        float dmin = INFINITY, dsum = 0.f, wind = 0.f;
+        for (int c0 = 0; c0 < m; c0 += kSetChunk) {
+            const int len = m - c0 < kSetChunk ? m - c0 : kSetChunk;
+            __syncthreads();
+            for (int k = threadIdx.x; k <= len; k += blockDim.x) {
+                const int src = k > 0 ? c0 + k - 1 : (c0 > 0 ? c0 - 1 : m - 1);
+                sh[k] = make_float2((float)(set[src].x - cr), (float)(set[src].y - ci));
+            }
+            __syncthreads();
+            if (!live) continue;
+            float2 prev = make_float2(sh[0].x - pr, sh[0].y - pi);
+            for (int k = 1; k <= len; ++k) {
+                const float2 cur = make_float2(sh[k].x - pr, sh[k].y - pi);
+                const float dc = sqrtf(cur.x * cur.x + cur.y * cur.y);
+                dsum += dc;
+                if (CLOSED) {
+                    // nearest point of the piece prev -> cur to the point (the origin here)
+                    const float ex = cur.x - prev.x, ey = cur.y - prev.y;
+                    const float ee = ex * ex + ey * ey;
+                    const float t = ee > 0.f ? fminf(fmaxf(-(prev.x * ex + prev.y * ey) / ee, 0.f), 1.f) : 0.f;
+                    const float qx = prev.x + t * ex, qy = prev.y + t * ey;
+                    dmin = fminf(dmin, sqrtf(qx * qx + qy * qy));
+                    // angle swept from prev to cur about the point
+                    wind += atan2f(prev.x * cur.y - prev.y * cur.x, prev.x * cur.x + prev.y * cur.y);
+                } else {
+                    dmin = fminf(dmin, dc);
+                }
+                prev = cur;
+            }
+        }
+        if (!live) continue;
         float v[64];
         // Fourier encoding of c = (x^, y^) in [-1, 1]^2: [c, sin 2^k c, cos 2^k c], k = 1..6
         const float cx = (float)((zr - xc) / hw), cy = (float)((zi - yc) / hh);
@@ -269,35 +361,16 @@ __global__ void k_point_features(double re_min, double im_min, double hx, double
             v[2 + 4 * (k - 1) + 2] = cxx;
             v[2 + 4 * (k - 1) + 3] = cyy;
         }
-        // distances (about the centroid, in units of the curve's radius R) and winding;
-        // dmin is the distance to the closed polyline through the samples (exact for a
-        // curve made of straight pieces, such as the segment of a kl = ku Grcar-type band,
-        // whose sensitive zone is a band of width about 2 eps around it)
-        const float pr = (float)(zr - cr), pi = (float)(zi - ci);
-        float dmin = INFINITY, dsum = 0.f, wind = 0.f;
-        float2 prev = make_float2(sym[T - 1].x - pr, sym[T - 1].y - pi);
-        for (int k = 0; k < T; ++k) {
-            const float2 cur = make_float2(sym[k].x - pr, sym[k].y - pi);
-            dsum += sqrtf(cur.x * cur.x + cur.y * cur.y);
-            // nearest point of the piece prev -> cur to the point (the origin here)
-            const float ex = cur.x - prev.x, ey = cur.y - prev.y;
-            const float ee = ex * ex + ey * ey;
-            const float t = ee > 0.f ? fminf(fmaxf(-(prev.x * ex + prev.y * ey) / ee, 0.f), 1.f) : 0.f;
-            const float qx = prev.x + t * ex, qy = prev.y + t * ey;
-            dmin = fminf(dmin, sqrtf(qx * qx + qy * qy));
-            // angle swept from prev to cur about the point
-            wind += atan2f(prev.x * cur.y - prev.y * cur.x, prev.x * cur.x + prev.y * cur.y);
-            prev = cur;
-        }
-        const float g1 = dmin / R, g3 = dsum / (float)T / R, g2 = sqrtf(pr * pr + pi * pi) / R;
+        const float g1 = dmin / R, g3 = dsum / (float)m / R, g2 = sqrtf(pr * pr + pi * pi) / R;
         v[26] = g1;
         v[27] = g2;
         v[28] = g3;
         v[29] = log10f(g1 + 1e-7f);
         v[30] = log10f(g3 + 1e-7f);
-        v[31] = rintf(wind / 6.28318530718f);
+        v[31] = CLOSED ? rintf(wind / 6.28318530718f) : 0.f;
         for (int k = 0; k < PSA_GLOBAL_FEATURES; ++k) v[32 + k] = gf[k];
-        // the distance to the curve against the level: log10(dmin / eps) (gf[24] = log10(eps / R))
+        // the distance to the curve (or set) against the level: log10(dmin / eps), with
+        // gf[24] = log10(eps / R)
         v[32 + PSA_GLOBAL_FEATURES] = v[29] - gf[24];
         __nv_bfloat16 *row = x + p * PSA_MLP_IN;
         for (int k = 0; k < kPointFeatures; ++k) row[k] = __float2bfloat16_rn(v[k]);
@@ -365,10 +438,20 @@ int psa_global_features(const double *stats, const double *sigma4, double eps, f
     return cudaGetLastError() == cudaSuccess ? PSA_OK : PSA_ECUDA;
 }
 
-int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
-                       const psa_c64 *symbol, const float *global, uint16_t *x, void *stream)
+int psa_point_set_stats(const psa_c64 *set, int32_t m, double *stats, void *stream)
 {
-    if (!g || !stats || !symbol || !global || !x || g->nx < 1 || g->ny < 1 || n_idx < 0 || (n_idx > 0 && !idx))
+    if (!set || !stats || m < 1) return PSA_EINVAL;
+    k_point_set_stats<<<1, NT, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const double2 *>(set), m,
+                                                                        stats);
+    return cudaGetLastError() == cudaSuccess ? PSA_OK : PSA_ECUDA;
+}
+
+int psa_point_features_set(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
+                           const psa_c64 *set, int32_t m, int32_t closed, const float *global, uint16_t *x,
+                           void *stream)
+{
+    if (!g || !stats || !set || !global || !x || g->nx < 1 || g->ny < 1 || n_idx < 0 || (n_idx > 0 && !idx) ||
+        m < 1 || (closed != 0 && closed != 1))
         return PSA_EINVAL;
     if (!(std::isfinite(g->re_min) && std::isfinite(g->re_max) && std::isfinite(g->im_min) &&
           std::isfinite(g->im_max)) ||
@@ -380,10 +463,22 @@ int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, con
     const double hx = g->nx > 1 ? (g->re_max - g->re_min) / (double)(g->nx - 1) : 0.0;
     const double hy = g->ny > 1 ? (g->im_max - g->im_min) / (double)(g->ny - 1) : 0.0;
     const int64_t blocks = (npts + 255) / 256 < 8192 ? (npts + 255) / 256 : 8192;
-    k_point_features<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        g->re_min, g->im_min, hx, hy, g->nx, g->ny, idx, npts, global, stats,
-        reinterpret_cast<const double2 *>(symbol), reinterpret_cast<__nv_bfloat16 *>(x));
+    const double2 *s = reinterpret_cast<const double2 *>(set);
+    __nv_bfloat16 *xb = reinterpret_cast<__nv_bfloat16 *>(x);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (closed)
+        k_point_features<true><<<(unsigned)blocks, 256, 0, st>>>(g->re_min, g->im_min, hx, hy, g->nx, g->ny, idx,
+                                                                 npts, global, stats, s, m, xb);
+    else
+        k_point_features<false><<<(unsigned)blocks, 256, 0, st>>>(g->re_min, g->im_min, hx, hy, g->nx, g->ny, idx,
+                                                                  npts, global, stats, s, m, xb);
     return cudaGetLastError() == cudaSuccess ? PSA_OK : PSA_ECUDA;
+}
+
+int psa_point_features(const psa_grid *g, const int32_t *idx, int64_t n_idx, const double *stats,
+                       const psa_c64 *symbol, const float *global, uint16_t *x, void *stream)
+{
+    return psa_point_features_set(g, idx, n_idx, stats, symbol, PSA_SYMBOL_SAMPLES, 1, global, x, stream);
 }
 
 int psa_region(const float *prob, float tau, int32_t nx, int32_t ny, int32_t radius, uint8_t *mask, void *stream)

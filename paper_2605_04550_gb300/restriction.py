@@ -56,23 +56,38 @@ class MatrixContext:
     stats: object   # CUDA float64 [STATS]
     symbol: object  # CUDA complex128 [SYMBOL_SAMPLES]
     glob: object    # CUDA float32 [GLOBAL_FEATURES]
+    #: CUDA complex128 [m]: a point set (the eigenvalues of A) that replaces the symbol
+    #: curve in the spectrum features, or None (the symbol curve)
+    spectrum: object = None
 
 
 def matrix_contexts(mats: Sequence[Tuple[object, int, int]], eps: float = EPS,
-                    opts: Optional[LanczosOpts] = None) -> List[MatrixContext]:
+                    opts: Optional[LanczosOpts] = None, spectra: Optional[Sequence[object]] = None
+                    ) -> List[MatrixContext]:
     """Global features of every matrix (bands already on the device). The four
     sigma_min probes (z = 0 and the centroid + 0.5, 1, 2) of all matrices run as
-    one batched call."""
+    one batched call. With ``spectra`` (one array of eigenvalues per matrix, host
+    or device), the spectrum features are the paper's own, taken over those
+    eigenvalues instead of the symbol curve (psa_point_set_stats)."""
     import torch
     lib = _native.load()
     dev = mats[0][0].device
     s = torch.cuda.current_stream(dev)
     stats = torch.empty((len(mats), _native.STATS), dtype=torch.float64, device=dev)
     symbol = torch.empty((len(mats), _native.SYMBOL_SAMPLES), dtype=torch.complex128, device=dev)
+    if spectra is not None and len(spectra) != len(mats):
+        raise ValueError("one eigenvalue array per matrix")
+    sets = [None] * len(mats)
     for m, (b, kl, ku) in enumerate(mats):
         A = _native.PsaBand(int(b.shape[1]), int(kl), int(ku), b.data_ptr())
         _native.check(lib.psa_matrix_stats(ctypes.byref(A), stats[m].data_ptr(), symbol[m].data_ptr(), s.cuda_stream),
                       "psa_matrix_stats")
+        if spectra is not None:
+            sets[m] = torch.as_tensor(spectra[m], dtype=torch.complex128, device=dev).reshape(-1).contiguous()
+            if sets[m].numel() < 1 or sets[m].numel() > 2**31 - 1:
+                raise ValueError("an eigenvalue array must hold 1 to 2^31 - 1 values")
+            _native.check(lib.psa_point_set_stats(sets[m].data_ptr(), int(sets[m].numel()), stats[m].data_ptr(),
+                                                  s.cuda_stream), "psa_point_set_stats")
     cen = stats[:, :2].cpu().numpy()  # the probe grids are host arguments
     entries = []
     for m, (b, kl, ku) in enumerate(mats):
@@ -89,7 +104,7 @@ def matrix_contexts(mats: Sequence[Tuple[object, int, int]], eps: float = EPS,
     for m in range(len(mats)):
         _native.check(lib.psa_global_features(stats[m].data_ptr(), sigma4[m].data_ptr(), float(eps),
                                               glob[m].data_ptr(), s.cuda_stream), "psa_global_features")
-    return [MatrixContext(b, kl, ku, stats[m], symbol[m], glob[m]) for m, (b, kl, ku) in enumerate(mats)]
+    return [MatrixContext(b, kl, ku, stats[m], symbol[m], glob[m], sets[m]) for m, (b, kl, ku) in enumerate(mats)]
 
 
 def point_features(ctx: MatrixContext, grid: Grid, idx=None, out=None):
@@ -107,9 +122,15 @@ def point_features(ctx: MatrixContext, grid: Grid, idx=None, out=None):
         raise ValueError("out must be a contiguous bfloat16 (npoints, IN) tensor")
     g = _grid_c(grid)
     s = torch.cuda.current_stream(dev)
-    _native.check(lib.psa_point_features(ctypes.byref(g), idx.data_ptr() if idx is not None else None,
-                                         n if idx is not None else 0, ctx.stats.data_ptr(), ctx.symbol.data_ptr(),
-                                         ctx.glob.data_ptr(), x.data_ptr(), s.cuda_stream), "psa_point_features")
+    ip, ni = (idx.data_ptr(), n) if idx is not None else (None, 0)
+    if ctx.spectrum is None:
+        _native.check(lib.psa_point_features(ctypes.byref(g), ip, ni, ctx.stats.data_ptr(), ctx.symbol.data_ptr(),
+                                             ctx.glob.data_ptr(), x.data_ptr(), s.cuda_stream), "psa_point_features")
+    else:
+        _native.check(lib.psa_point_features_set(ctypes.byref(g), ip, ni, ctx.stats.data_ptr(),
+                                                 ctx.spectrum.data_ptr(), int(ctx.spectrum.numel()), 0,
+                                                 ctx.glob.data_ptr(), x.data_ptr(), s.cuda_stream),
+                      "psa_point_features_set")
     return x
 
 
@@ -176,7 +197,8 @@ def recall_metrics(truth: np.ndarray, pred_region: np.ndarray) -> dict:
             "sensitive_fraction": float(t.mean())}
 
 
-#: column of a feature row holding log10(distance to the symbol polyline / eps)
+#: column of a feature row holding log10(distance to the symbol polyline, or to the
+#: nearest eigenvalue with eigenvalue features, / eps)
 NEAR_COL = 32 + _native.GLOBAL_FEATURES
 #: points within NEAR_FACTOR * eps of the symbol curve always enter the region
 NEAR_FACTOR = 2.0
@@ -189,7 +211,9 @@ def near_curve(x, grid: Grid, eps: float, coarse: bool = False):
     Lambda_eps once n is large (sigma_min(zI - A) -> 0 on it), and sigma_min is
     1-Lipschitz in z, so these points are sensitive or next to the zone; the rule
     catches the thin zone of nearly normal matrices (a kl = ku Grcar-type band), which
-    is a band of width 2 eps about the spectrum that coarse training labels rarely hit."""
+    is a band of width 2 eps about the spectrum that coarse training labels rarely hit.
+    With eigenvalue features the column holds the distance to the nearest eigenvalue,
+    and sigma_min(zI - A) <= |z - lambda| for every eigenvalue lambda."""
     h = max((grid.re_max - grid.re_min) / max(grid.nx - 1, 1), (grid.im_max - grid.im_min) / max(grid.ny - 1, 1))
     reach = NEAR_FACTOR * eps + (4.25 * h if coarse else 0.0)
     return x[:, NEAR_COL].float() <= float(np.log10(reach / eps))
@@ -207,8 +231,12 @@ def _grow(flag):
 class Restriction:
     """The trained classifier with its calibrated thresholds."""
 
-    def __init__(self, device="cuda", seed: int = 0, eps: float = EPS, net: str = "mlp"):
+    def __init__(self, device="cuda", seed: int = 0, eps: float = EPS, net: str = "mlp",
+                 features: str = "symbol"):
+        if features not in ("symbol", "eigen"):
+            raise ValueError("features must be 'symbol' (the symbol curve) or 'eigen' (eigenvalues)")
         self.net = net
+        self.features = features
         self.theta = mlp.init_theta(seed, device, net)
         self.device = device
         self.eps = eps
@@ -221,7 +249,7 @@ class Restriction:
         """Parameters, threshold and calibration summary to an .npz file."""
         import json
         th = self.theta.detach().cpu().numpy().astype(np.float32)
-        info = {"tau": self.tau, "eps": self.eps, "net": self.net, "meta": meta or {},
+        info = {"tau": self.tau, "eps": self.eps, "net": self.net, "features": self.features, "meta": meta or {},
                 "calibration": {k: v for k, v in self.calibration.items() if k != "table"}}
         np.savez(path, theta=th, info=np.frombuffer(json.dumps(info).encode(), dtype=np.uint8))
 
@@ -235,7 +263,7 @@ class Restriction:
         net = info.get("net", "mlp")
         if th.shape != (mlp.nparam(net),) or th.dtype != np.float32:
             raise ValueError("parameter vector of the wrong size")
-        r = cls(device, eps=float(info["eps"]), net=net)
+        r = cls(device, eps=float(info["eps"]), net=net, features=info.get("features", "symbol"))
         r.theta = torch.as_tensor(th, device=device)
         r.tau = float(info["tau"])
         r.calibration = info.get("calibration", {})
@@ -243,24 +271,37 @@ class Restriction:
         return r
 
     # ------------------------------------------------------------ training
-    def build_training_set(self, mats, grids, rng: np.random.Generator, opts: LanczosOpts = LABEL_OPTS):
+    def build_training_set(self, mats, grids, rng: np.random.Generator, opts: LanczosOpts = LABEL_OPTS,
+                           spectra=None, labels=None):
         """Features and labels of the training matrices, balanced per matrix: all
-        positives and max(10 n_pos, 200) negatives (fewer if the grid has fewer)."""
+        positives and max(10 n_pos, 200) negatives (fewer if the grid has fewer).
+        ``spectra``: the eigenvalues of each matrix, for a classifier on eigenvalue
+        features. ``labels``: the ``last_labels`` of an earlier call on the same
+        matrices and grids, to reuse its sigma_min labels (with an rng in the same
+        state the same points are drawn)."""
         import torch
+        if (spectra is not None) != (self.features == "eigen"):
+            raise ValueError("spectra are required exactly for a classifier on eigenvalue features")
         dev = mats[0][0].device
         t0 = time.perf_counter()
-        ctxs = matrix_contexts(mats, self.eps)
+        ctxs = matrix_contexts(mats, self.eps, spectra=spectra)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
-        plan, sig, st = labels_batched(mats, grids, self.eps, opts, with_status=True)
-        lab = (sig <= self.eps).to(torch.uint8).cpu().numpy()
+        if labels is None:
+            plan, sig, st = labels_batched(mats, grids, self.eps, opts, with_status=True)
+            offsets = list(plan.offsets)
+            lab = (sig <= self.eps).to(torch.uint8).cpu().numpy()
+            stc = np.bincount(st.cpu().numpy().astype(np.int64), minlength=6)
+            counts = {str(k): int(v) for k, v in enumerate(stc) if v}
+        else:
+            offsets, lab, counts = labels
+        self.last_labels = (offsets, lab, counts)
         t2 = time.perf_counter()
-        stc = np.bincount(st.cpu().numpy().astype(np.int64), minlength=6)
-        self.timing = {"contexts_s": t1 - t0, "labels_s": t2 - t1, "label_points": int(sig.numel()),
-                       "label_status_counts": {str(k): int(v) for k, v in enumerate(stc) if v}}
+        self.timing = {"contexts_s": t1 - t0, "labels_s": t2 - t1, "label_points": int(lab.size),
+                       "label_status_counts": counts}
         xs, ys = [], []
         for m, (ctx, g) in enumerate(zip(ctxs, grids)):
-            o = plan.offsets[m]
+            o = offsets[m]
             y = lab[o:o + g.npoints]
             pos = np.flatnonzero(y)
             neg = np.flatnonzero(y == 0)
@@ -314,6 +355,11 @@ class Restriction:
         return self.history
 
     # ----------------------------------------------------------- inference
+    def _check_ctx(self, ctx: MatrixContext):
+        if (ctx.spectrum is not None) != (self.features == "eigen"):
+            raise ValueError(f"this classifier takes {self.features} features; build the context "
+                             + ("with spectra=" if self.features == "eigen" else "without spectra"))
+
     def predict(self, ctx: MatrixContext, grid: Grid, hierarchical: bool = True, tau: Optional[float] = None):
         """Probability map (ny, nx) float32 on the device. Hierarchical: the coarse
         stride-4 grid first; a coarse cell is refined (its 4 x 4 fine points
@@ -321,6 +367,7 @@ class Restriction:
         reaches the 80th percentile of the coarse map or the decision threshold,
         whichever is lower; other points get 0."""
         import torch
+        self._check_ctx(ctx)
         dev = ctx.bands.device
         nx, ny = grid.nx, grid.ny
         if not hierarchical:

@@ -181,3 +181,75 @@ def test_shipped_classifier_reaches_recall_on_a_fresh_matrix(net):
         np.testing.assert_array_equal(out.sigma.cpu().numpy()[m], full.sigma.cpu().numpy()[m])
         met = restriction.recall_metrics(full.sigma.cpu().numpy() <= restriction.EPS, m)
         assert met["recall"] >= 0.99, (n, met)
+
+
+def test_eigenvalue_features_match_the_feature_oracle():
+    """The paper's own spectrum features (Sec. 3.1, Table "matrix"; Eq. (dist)) over the
+    eigenvalues: statistics, global features and point rows against the oracle."""
+    b, kl, ku, a = inputs.random_toeplitz(150, 2, 5, seed=11)
+    b = b + 0.01 * np.random.default_rng(0).standard_normal(b.shape)
+    b = inputs._zero_outside(b.astype(np.complex128), 150, kl, ku)
+    lam = np.linalg.eigvals(_dense(b, kl, ku))
+    ctx = restriction.matrix_contexts([(_t(b), kl, ku)], spectra=[lam])[0]
+    st0, _ = FO.matrix_stats(b, kl, ku)
+    ref = FO.point_set_stats(st0, lam)
+    st = ctx.stats.cpu().numpy()
+    np.testing.assert_allclose(st, ref, rtol=1e-10, atol=1e-13 * np.abs(ref).max())
+    cen = complex(ref[0], ref[1])
+    s4, _, _ = oracle.sigma_min_banded(b, kl, ku, np.array([0.0, cen + 0.5, cen + 1.0, cen + 2.0]),
+                                       k_max=300, tol=1e-6)
+    gl = ctx.glob.cpu().numpy()
+    np.testing.assert_allclose(gl, FO.global_features(ref, s4, restriction.EPS), rtol=2e-5, atol=2e-5)
+    grid = inputs.toeplitz_symbol_grid(a, kl, ku, 23, 17)
+    x = restriction.point_features(ctx, grid).float().cpu().numpy()
+    xr = FO.point_features(grid, st, lam, gl.astype(np.float64), np.arange(grid.npoints), closed=False)
+    np.testing.assert_allclose(x, xr, rtol=1e-2, atol=2e-2)
+    assert np.all(x[:, 31] == 0)
+
+
+@pytest.mark.parametrize("closed", [0, 1])
+def test_point_features_over_a_set_of_several_chunks(closed):
+    """A set of 5000 points passes through shared memory in chunks of 2048 (two full
+    chunks and a ragged one); the closed polyline joins the chunks and wraps around."""
+    import ctypes
+    lib = _native.load()
+    rng = np.random.default_rng(8)
+    b, kl, ku = inputs.grcar(120)
+    ctx = restriction.matrix_contexts([(_t(b), kl, ku)])[0]
+    pts = np.exp(2j * np.pi * np.sort(rng.random(5000))) * (1.0 + 0.3 * rng.random(5000)) + 1.0
+    grid = inputs.Grid(-1.0, 3.0, -2.0, 2.0, 31, 29)
+    sel = np.sort(rng.choice(grid.npoints, 60, replace=False)).astype(np.int32)
+    idx = torch.as_tensor(sel, device=DEV)
+    dp = _t(pts)
+    x = torch.empty((sel.size, mlp.IN), dtype=torch.bfloat16, device=DEV)
+    g = restriction._grid_c(grid)
+    _native.check(lib.psa_point_features_set(ctypes.byref(g), idx.data_ptr(), sel.size, ctx.stats.data_ptr(),
+                                             dp.data_ptr(), pts.size, closed, ctx.glob.data_ptr(), x.data_ptr(),
+                                             torch.cuda.current_stream().cuda_stream), "psa_point_features_set")
+    xr = FO.point_features(grid, ctx.stats.cpu().numpy(), pts, ctx.glob.cpu().numpy().astype(np.float64), sel,
+                           closed=bool(closed))
+    np.testing.assert_allclose(x.float().cpu().numpy(), xr, rtol=1e-2, atol=2e-2)
+    if closed:
+        np.testing.assert_array_equal(x.float().cpu().numpy()[:, 31], xr[:, 31])
+
+
+def test_classifier_on_eigenvalue_features_trains_and_predicts():
+    rng = np.random.default_rng(0)
+    tr = inputs.restriction_matrices(24, seed=5, n_min=150, n_max=300, nx=16, ny=16)
+    mats = [(_t(b), kl, ku) for b, kl, ku, _, _ in tr]
+    spectra = [np.linalg.eigvals(_dense(b, kl, ku)) for b, kl, ku, _, _ in tr]
+    grids = [g for *_, g, _ in tr]
+    sym = restriction.Restriction(DEV, seed=2, net="dual")
+    x0, y0, _ = sym.build_training_set(mats, grids, np.random.default_rng(1))
+    eig = restriction.Restriction(DEV, seed=2, net="dual", features="eigen")
+    x1, y1, ctxs = eig.build_training_set(mats, grids, np.random.default_rng(1), spectra=spectra,
+                                          labels=sym.last_labels)
+    # the same labels and the same drawn points; the Fourier columns agree, the spectrum ones not
+    assert torch.equal(y0, y1)
+    assert torch.equal(x0[:, :26], x1[:, :26]) and not torch.equal(x0[:, 26:61], x1[:, 26:61])
+    hist = eig.train(x1, y1, rng, epochs=4, patience=2)
+    assert np.isfinite(hist[-1]["val_loss"])
+    p = eig.predict(ctxs[0], grids[0]).cpu().numpy()
+    assert p.shape == (grids[0].ny, grids[0].nx) and np.all((p >= 0) & (p <= 1))
+    with pytest.raises(ValueError):
+        sym.predict(ctxs[0], grids[0])  # a symbol-feature classifier refuses eigenvalue contexts

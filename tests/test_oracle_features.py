@@ -87,3 +87,46 @@ def test_point_feature_identities():
     z = oracle.grid_points(grid).ravel()
     assert np.all(x[:, 26] <= np.abs(f[None, :] - z[:, None]).min(axis=1) / st[2] + 1e-15)
     assert np.all(x[:, 61:] == 0)
+
+
+def test_point_set_stats_of_a_symmetric_cross():
+    # four points c +- a, c +- i b about the centroid c: means 0, extremes +-a and +-b
+    st, _ = F.matrix_stats(_toeplitz(20, [0.5, 1.0 + 2.0j, 0.0], 1, 1), 1, 1)
+    c = complex(st[0], st[1])
+    assert np.isclose(c, 1.0 + 2.0j)
+    a, b = 0.7, 0.3
+    out = F.point_set_stats(st, [c + a, c - a, c + 1j * b, c - 1j * b])
+    assert np.isclose(out[2], a) and np.isclose(out[21], b)
+    np.testing.assert_allclose(out[[13, 17]], 0.0, atol=1e-15)
+    np.testing.assert_allclose(out[[15, 16, 19, 20]], [-a, a, -b, b], atol=1e-15)
+    assert np.isclose(out[14], np.sqrt(a * a / 2)) and np.isclose(out[18], np.sqrt(b * b / 2))
+    # every entry that does not describe the spectrum is kept
+    keep = [k for k in range(24) if k != 2 and not 13 <= k <= 21]
+    np.testing.assert_array_equal(out[keep], st[keep])
+    # the symbol samples as the set give back the symbol statistics
+    st2, f2 = F.matrix_stats(_toeplitz(20, [0.5, 1.0, 2.0], 1, 1), 1, 1)
+    np.testing.assert_allclose(F.point_set_stats(st2, f2), st2, rtol=1e-13, atol=1e-15)
+
+
+def test_point_set_features_of_a_ring_and_a_single_point():
+    grid = inputs.Grid(-1.0, 1.0, -1.0, 1.0, 5, 5)  # grid point 12 is z = 0
+    b = _toeplitz(30, [0.0, 1.0], 0, 1)  # centroid 0
+    st, _ = F.matrix_stats(b, 0, 1)
+    r = 0.4
+    ring = r * np.exp(2j * np.pi * np.arange(64) / 64)
+    sst = F.point_set_stats(st, ring)
+    g = F.global_features(sst, np.array([0.1, 0.2, 0.3, 0.4]), 0.01)
+    x = F.point_features(grid, sst, ring, g, [12], closed=False)[0]
+    # every point of the ring is r from its centre, and R = r: g1 = g3 = 1
+    assert np.isclose(x[26], 1.0) and np.isclose(x[28], 1.0) and x[31] == 0
+    # the polyline through the same points is closer (its chords cut inside) and winds once
+    xc = F.point_features(grid, sst, ring, g, [12], closed=True)[0]
+    assert xc[26] < x[26] and xc[31] == 1
+    # a single eigenvalue: g1 = g3 = |z - lambda| / R at every point
+    lam = 0.25 - 0.5j
+    s1 = F.point_set_stats(st, [lam])
+    g1 = F.global_features(s1, np.array([0.1, 0.2, 0.3, 0.4]), 0.01)
+    xs = F.point_features(grid, s1, np.array([lam]), g1, np.arange(25), closed=False)
+    z = oracle.grid_points(grid).ravel()
+    np.testing.assert_allclose(xs[:, 26], np.abs(z - lam) / abs(lam), rtol=1e-14)
+    np.testing.assert_allclose(xs[:, 28], xs[:, 26], rtol=0, atol=0)
