@@ -69,6 +69,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
             zi = z.y;
         }
         const bool singular = band_lu<KL, KU>(p, M, rows, pivs, Aw, lane, zr, zi, bad_input);
+        // Lanes leave the Lanczos loops at their own step counts. Without a barrier the
+        // lanes that are done would run ahead into the next phase while the others still
+        // iterate, and the warp would issue both phases' FP64 instructions one after the
+        // other (each costs the whole warp's FP64 slot whatever the active lanes): the
+        // warp is brought back together after the first pass and around the replay.
+        const unsigned live = __ballot_sync(0xffffffffu, have && !singular && !bad_input);
 
         double sigma = 0.0;
         int status = bad_input ? 3 : 1;
@@ -80,7 +86,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
             LzState st;
             double theta = 0.0;
             status = lanczos_sigma<KL, KU>(p, M, rows, pivs, Ta, Tb, st, sigma, ksteps, theta);
+            __syncwarp(live);
             ok = (status == 0 || status == 2) && sigma > 0.0 && ksteps >= 1;
+            const unsigned okm = __ballot_sync(live, ok);
             if (ok) {
                 // ---- 1. s = top eigenvector of T_k: two steps of inverse iteration on M = x I - T_k
                 const int k = ksteps;
@@ -118,11 +126,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
                 for (int i = 1; i < k; ++i) Tc[(int64_t)i * TS] /= sqrt(Tb[(int64_t)(i - 1) * TS]);
 
                 // ---- 2. second pass: y = sum_j c_j v_j into FY (same recurrence, same bits)
+                __syncwarp(okm);
                 LzState st2;
                 for (int j = 1; j <= k; ++j) {
                     double a2;
                     (void)lanczos_step<KL, KU, true>(p, M, rows, pivs, Ta, Tb, j, st2, a2, Tc[(int64_t)(j - 1) * TS], j == k);
                 }
+                __syncwarp(okm);
 
                 // ---- 3. u = y / |y| (kept in FY), x = B^{-1} (2^-e1 u) in FX, v = x / |x|
                 double ny = 0.0;
@@ -193,6 +203,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sigma_min_grad(const KParams p)
                 wgt = p.gweight ? p.gweight[pt] : 0.0;
             }
         }
+        __syncwarp();
         // ---- the singular pair itself (u, v = x / |x|), element-major so that a warp's
         //      32 points write 32 consecutive values of each row
         if (p.u_out && have) {

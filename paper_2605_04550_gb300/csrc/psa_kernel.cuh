@@ -329,6 +329,7 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, const Mat &M, char
     auto pf_lvec = [&](int j, bool with_fx) {
         l2_prefetch(wb + (int64_t)j * RB + (KW + 1) * 512, with_fx ? kLBytes + 512u : kLBytes);
         if (KL > 0) l2_prefetch(wb + (int64_t)j * RB + p.piv_offset, 32u);
+        if (ACC && !with_fx) l2_prefetch(wb + (int64_t)j * RB + SH::FY * 512, 512u);  // Ritz vector, sweep (a)
     };
     auto pf_u = [&](int j) {
         l2_prefetch(wb + (int64_t)j * RB, kUBytes);
@@ -340,27 +341,27 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, const Mat &M, char
     double b2 = 0.0;
     {
         double2 X[KL + 1];
-        auto make_v = [&](int ii, double2 w, double2 vp) -> double2 {
+        // y: the Ritz vector's current value at row ii (ACC only), loaded with the row's
+        // other operands one row ahead
+        auto make_v = [&](int ii, double2 w, double2 vp, double2 y) -> double2 {
             const double2 v = first ? w : make_double2(fma(-st.acoef, vp.x, w.x), fma(-st.acoef, vp.y, w.y));
             b2 = fma(v.x, v.x, fma(v.y, v.y, b2));
             FLD(ii, fcur) = v;
-            if (ACC) {  // Ritz vector: y += yc v_k
-                const double2 y = first ? make_double2(0.0, 0.0) : FLD(ii, SH::FY);
-                FLD(ii, SH::FY) = make_double2(fma(yc, v.x, y.x), fma(yc, v.y, y.y));
-            }
+            if (ACC) FLD(ii, SH::FY) = make_double2(fma(yc, v.x, y.x), fma(yc, v.y, y.y));  // y += yc v_k
             return v;
         };
-        auto load_w = [&](int ii, double2 &w, double2 &vp) {
+        auto load_w = [&](int ii, double2 &w, double2 &vp, double2 &y) {
             if (first) { w = __ldg(&M.q1[ii]); vp = make_double2(0.0, 0.0); }
             else { w = FLD(ii, fcur); vp = FLD(ii, fprv); }
+            y = (ACC && !first) ? FLD(ii, SH::FY) : make_double2(0.0, 0.0);
         };
 #pragma unroll
         for (int r = 0; r < KL; ++r) {
             X[r] = make_double2(0.0, 0.0);
-            if (r < n) { double2 w, vp; load_w(r, w, vp); X[r] = make_v(r, w, vp); }
+            if (r < n) { double2 w, vp, y; load_w(r, w, vp, y); X[r] = make_v(r, w, vp, y); }
         }
         // row j needs pivot j, multipliers of column j and v_{j+KL}; prefetch row j+1
-        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0);
+        double2 nl[KL + 1], nw = make_double2(0.0, 0.0), nvp = make_double2(0.0, 0.0), nyr = make_double2(0.0, 0.0);
         int npv = 0;
         auto load_a = [&](int j) {
             if (KL > 0) {
@@ -368,7 +369,7 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, const Mat &M, char
 #pragma unroll
                 for (int r = 1; r <= KL; ++r) nl[r] = FLD(j, KW + r);
             }
-            if (j + KL < n) load_w(j + KL, nw, nvp);
+            if (j + KL < n) load_w(j + KL, nw, nvp, nyr);
         };
         if (pf_lane)
             for (int j = 0; j < kPfRows && j < n; ++j) pf_lvec(j, false);
@@ -380,9 +381,9 @@ __device__ __forceinline__ int lanczos_step(const KParams &p, const Mat &M, char
 #pragma unroll
             for (int r = 1; r <= KL; ++r) cl[r] = nl[r];
             const int cpv = npv;
-            const double2 cw = nw, cvp = nvp;
+            const double2 cw = nw, cvp = nvp, cy = nyr;
             if (j + 1 < n) load_a(j + 1);
-            X[KL] = (j + KL < n) ? make_v(j + KL, cw, cvp) : make_double2(0.0, 0.0);
+            X[KL] = (j + KL < n) ? make_v(j + KL, cw, cvp, cy) : make_double2(0.0, 0.0);
             if (KL > 0) {
 #pragma unroll
                 for (int r = 1; r <= KL; ++r) {
