@@ -593,7 +593,7 @@ def run_differentiation(args):
             "config": {"workload": "Grcar-type n=4000 kl=1 ku=3, band entries + N(0,1e-2) (seed 0), "
                                    f"{grid.nx}x{grid.ny} grid over [-1,3]x[-3.5,3.5] (points in 8x4 tile order), "
                                    "grad_z and band gradient (unit weights), Lanczos tol 1e-13"},
-            "mean_lanczos_steps": float(steps.mean()),
+            "mean_lanczos_steps": float(steps.mean()), "max_lanczos_steps": int(steps.max()),
             "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
                          "achieved_two_pass": two_pass / (ms * 1e-3) / 1e12,
                          "frac_two_pass": two_pass / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,

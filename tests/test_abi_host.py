@@ -143,3 +143,20 @@ def _call_static(lib, *, n=10, kl=1, ku=1, bands=1 << 20, grid=(-1.0, 1.0, -1.0,
 def test_static_entry_point_rejects_on_the_host(lib, kw, code):
     # every rejection happens before any device call (no GPU here)
     assert _call_static(lib, **kw) == code
+
+
+@pytest.mark.parametrize("m,closed,null", [(0, 0, None), (-3, 1, None), (5, 2, None), (5, -1, None),
+                                           (5, 0, "set"), (5, 1, "global"), (5, 0, "x")])
+def test_point_features_over_a_set_rejects_on_the_host(lib, m, closed, null):
+    g = _native.PsaGrid(-1.0, 1.0, -1.0, 1.0, 4, 4)
+    p = {"set": 1 << 20, "global": 1 << 21, "x": 1 << 22}
+    if null:
+        p[null] = None
+    rc = lib.psa_point_features_set(ctypes.byref(g), None, 0, 1 << 23, p["set"], m, closed, p["global"], p["x"], None)
+    assert rc == _native.PSA_EINVAL
+
+
+def test_point_set_stats_rejects_on_the_host(lib):
+    assert lib.psa_point_set_stats(1 << 20, 0, 1 << 21, None) == _native.PSA_EINVAL
+    assert lib.psa_point_set_stats(None, 4, 1 << 21, None) == _native.PSA_EINVAL
+    assert lib.psa_point_set_stats(1 << 20, 4, None, None) == _native.PSA_EINVAL
