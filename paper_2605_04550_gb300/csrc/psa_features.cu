@@ -15,6 +15,12 @@
 // per grid point: the Fourier encoding of the normalised coordinates, the
 // distances to the centroid and to the symbol curve, the winding number of the
 // curve about the point, and the global features.
+//
+// The paper's own spectrum features are available too: psa_point_set_stats takes
+// the statistics over a point set (the eigenvalues of A from a dense eigensolver,
+// supplied by the caller), and the per-point kernel runs over any set, as a
+// closed polyline (the symbol samples) or as a point set (distance to the
+// nearest eigenvalue, Eq. (dist)).
 #include <cmath>
 #include <cstdint>
 #include <cuda_bf16.h>
