@@ -608,6 +608,45 @@ def run_differentiation(args):
     return 0
 
 
+def run_grad_case(args):
+    """Small case for profiler captures of the gradient kernel: sigma_min on a grid and then
+    sigma_min_grad (with unit weights) on the same points in tile order, one call each.
+    Grcar-type n = 300 + N(0, 1e-2) band noise (seed 0), 200 x 200 grid over
+    [-1, 3] x [-3.5, 3.5]; about 3 GB of workspace, freed between the two calls."""
+    import torch
+    import paper_2605_04550_gb300 as psa
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    b, kl, ku = inputs.grcar_perturbed(300, seed=0)
+    grid = inputs.Grid(-1.0, 3.0, -3.5, 3.5, 200, 200)
+    n, N = b.shape[1], grid.npoints
+    bt = torch.as_tensor(b, device=dev)
+    xs = grid.re_min + np.arange(grid.nx) * ((grid.re_max - grid.re_min) / (grid.nx - 1))
+    ys = grid.im_min + np.arange(grid.ny) * ((grid.im_max - grid.im_min) / (grid.ny - 1))
+    order = psa.tile_order(np.arange(N), grid.nx).astype(np.int64)
+    z = torch.as_tensor((xs[None, :] + 1j * ys[:, None]).ravel()[order], device=dev)
+    w = torch.ones(N, dtype=torch.float64, device=dev)
+    opts = psa.LanczosOpts()
+    pif = psa.default_points_in_flight(n, kl, ku, N)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ws = psa.Workspace(n, kl, ku, pif, opts, device=dev, npoints=N)
+    e[0].record()
+    o = psa.sigma_min(bt, kl, ku, grid, opts=opts, workspace=ws)
+    e[1].record()
+    torch.cuda.synchronize(dev)
+    del ws
+    torch.cuda.empty_cache()
+    gws = psa.GradWorkspace(n, kl, ku, pif, opts, device=dev)
+    e[2].record()
+    r = psa.sigma_min_grad(bt, kl, ku, z, weight=w, opts=opts, workspace=gws)
+    e[3].record()
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"case": "grad300", "n": n, "points": N, "sigma_min_ms": e[0].elapsed_time(e[1]),
+                      "sigma_min_grad_ms": e[2].elapsed_time(e[3]), "mean_lanczos_steps": float(o.steps.float().mean()),
+                      "grad_mean_lanczos_steps": float(r.steps.float().mean())}), flush=True)
+    return 0
+
+
 def run_batched(args):
     """Batch workload: 256 seeded matrices (n log-uniform in [200, 8000], kl 1..4, ku 1..8,
     Grcar-type or random Toeplitz with 1e-3 band noise), each on its own 128 x 128 grid,
@@ -1098,10 +1137,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100", "grid2000"],
+    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100", "grid2000", "grad300"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures; "
                          "grcar100: the Grcar n = 100 workload (small-order profile); grid2000: the "
-                         "benchmark workload's grid timing alone (full-size profiles)")
+                         "benchmark workload's grid timing alone (full-size profiles); grad300: sigma_min "
+                         "and the gradient kernel on the same 40 000 points (gradient profiles)")
     ap.add_argument("--workload", default="grid",
                     choices=["grid", "differentiation", "batched", "restriction", "classifier", "features"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
@@ -1127,6 +1167,8 @@ def main():
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "grad300":
+        return run_grad_case(args)
     if args.workload == "differentiation":
         return run_differentiation(args)
     if args.workload == "batched":
