@@ -647,6 +647,41 @@ def run_grad_case(args):
     return 0
 
 
+def run_fp64_probe(args):
+    """The FP64 unit's rates (psa_probe_fp64): DFMA against warps per SM, dependent chains
+    and active lanes, and DADD, DMUL, division and square root at full occupancy. Rates
+    are lane-operations per clock per SM at the sampled SM clock."""
+    import ctypes
+    import torch
+    from paper_2605_04550_gb300 import _native
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = _native.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    st = torch.cuda.current_stream(dev).cuda_stream
+    names = ["dfma", "dadd", "dmul", "div", "sqrt"]
+    cases = [(0, w, 32, c) for w in (1, 2, 4, 8, 16) for c in (1, 8)]
+    cases += [(0, w, 1, 8) for w in (4, 16)] + [(0, 4, 1, 1)]
+    cases += [(op, 16, 32, 8) for op in (1, 2, 3, 4)]
+    rows = []
+    with ClockSampler(0) as clk:
+        for op, w, a, c in cases:
+            # about 2e9 lane-operations at 32 active lanes (a few ms at the peak); the same
+            # iterations with one active lane
+            iters = max(64, int(2e9 / (sms * w * 32 * c)) // (8 if op >= 3 else 1))
+            r = ctypes.c_double(0.0)
+            _native.check(lib.psa_probe_fp64(op, w, a, c, iters, ctypes.byref(r), st), "psa_probe_fp64")
+            rows.append({"op": names[op], "warps_per_sm": w, "active_lanes": a, "chains": c,
+                         "lane_ops_per_s": r.value})
+    mhz = clk.summary().get("sm_mhz") or 2070.0
+    for row in rows:
+        row["lane_ops_per_clock_per_sm"] = row["lane_ops_per_s"] / (sms * mhz * 1e6)
+        # warp instructions per clock per SM: what an instruction costs whatever its active lanes
+        row["warp_inst_per_clock_per_sm"] = row["lane_ops_per_clock_per_sm"] / row["active_lanes"]
+    print(json.dumps({"case": "fp64probe", "sms": sms, "clocks": clk.summary(), "rows": rows}), flush=True)
+    return 0
+
+
 def run_batched(args):
     """Batch workload: 256 seeded matrices (n log-uniform in [200, 8000], kl 1..4, ku 1..8,
     Grcar-type or random Toeplitz with 1e-3 band noise), each on its own 128 x 128 grid,
@@ -1137,11 +1172,13 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="mid", choices=["mid", "small", "grcar100", "grid2000", "grad300"],
+    ap.add_argument("--case", default="mid",
+                    choices=["mid", "small", "grcar100", "grid2000", "grad300", "fp64probe"],
                     help="mid: the benchmark workload; small: reduced case for profiler captures; "
                          "grcar100: the Grcar n = 100 workload (small-order profile); grid2000: the "
                          "benchmark workload's grid timing alone (full-size profiles); grad300: sigma_min "
-                         "and the gradient kernel on the same 40 000 points (gradient profiles)")
+                         "and the gradient kernel on the same 40 000 points (gradient profiles); "
+                         "fp64probe: the FP64 unit's rates (psa_probe_fp64)")
     ap.add_argument("--workload", default="grid",
                     choices=["grid", "differentiation", "batched", "restriction", "classifier", "features"],
                     help="grid: the benchmark line; differentiation: the adjoint workload; "
@@ -1169,6 +1206,8 @@ def main():
         return run_reference(args)
     if args.case == "grad300":
         return run_grad_case(args)
+    if args.case == "fp64probe":
+        return run_fp64_probe(args)
     if args.workload == "differentiation":
         return run_differentiation(args)
     if args.workload == "batched":

@@ -565,6 +565,16 @@ int psa_tile_slots(const uint8_t *mask, int32_t nx, int32_t ny, int32_t *slot, v
  * Errors: PSA_EINVAL, PSA_ECUDA. */
 int psa_probe_dfma_rate(int32_t iters, double *dfma_per_s, void *stream);
 
+/* FP64 micro-benchmark behind the roofline and the one-lane-per-point layout:
+ * one block of warps_per_sm (1..32) warps per SM; in each warp the first
+ * active_lanes (1..32) lanes run `chains` (1 or 8) independent chains of `iters`
+ * (1..2^24) operations `op`: 0 DFMA, 1 DADD, 2 DMUL, 3 division, 4 square root.
+ * Runs a warm-up and a timed launch on `stream`, synchronises, and returns
+ * lane-operations per second (SMs x warps x active lanes x chains x iters /
+ * time) in *lane_ops_per_s. Errors: PSA_EINVAL, PSA_ECUDA. */
+int psa_probe_fp64(int32_t op, int32_t warps_per_sm, int32_t active_lanes, int32_t chains, int32_t iters,
+                   double *lane_ops_per_s, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

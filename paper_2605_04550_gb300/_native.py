@@ -52,6 +52,7 @@ EXPORTS = (
     "psa_region",
     "psa_tile_slots",
     "psa_probe_dfma_rate",
+    "psa_probe_fp64",
 )
 
 SYMBOL_SAMPLES, STATS, GLOBAL_FEATURES = 256, 24, 28
@@ -182,6 +183,8 @@ def load(path: str | None = None):
         lib.psa_tile_slots.argtypes = [vp, i32, i32, vp, vp]
         lib.psa_probe_dfma_rate.restype = ctypes.c_int
         lib.psa_probe_dfma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
+        lib.psa_probe_fp64.restype = ctypes.c_int
+        lib.psa_probe_fp64.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(dbl), vp]
         _lib = lib
         return lib
 
