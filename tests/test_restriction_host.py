@@ -46,3 +46,37 @@ def test_hierarchical_mask_keeps_flagged_cells_and_neighbours():
             if keep[i, j]:
                 kept_cells.add((i // 4, j // 4))
     assert kept_cells <= {(a, b) for a in (1, 2, 3) for b in (2, 3, 4)}
+
+
+def test_feature_kind_is_checked_and_survives_save_and_load(tmp_path):
+    """A classifier remembers whether it takes symbol-curve or eigenvalue features: the
+    kind is saved with it, and a context of the other kind is refused before any kernel."""
+    pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        restriction.Restriction("cpu", features="eigenvalues")
+    eig = restriction.Restriction("cpu", net="dual", features="eigen")
+    path = str(tmp_path / "eig.npz")
+    eig.save(path)
+    back = restriction.Restriction.load(path, "cpu")
+    assert back.features == "eigen" and back.net == "dual"
+    sym = restriction.Restriction("cpu", net="mlp")
+    assert sym.features == "symbol"
+    ctx_sym = restriction.MatrixContext(None, 1, 1, None, None, None)
+    ctx_eig = restriction.MatrixContext(None, 1, 1, None, None, None, spectrum=object())
+    with pytest.raises(ValueError):
+        sym._check_ctx(ctx_eig)
+    with pytest.raises(ValueError):
+        eig._check_ctx(ctx_sym)
+    sym._check_ctx(ctx_sym)
+    eig._check_ctx(ctx_eig)
+    with pytest.raises(ValueError):  # spectra exactly for the eigenvalue kind
+        sym.build_training_set([(None, 1, 1)], [None], np.random.default_rng(0), spectra=[np.zeros(3)])
+
+
+@pytest.mark.parametrize("net", ["mlp", "dual"])
+def test_shipped_classifiers_take_symbol_features(net):
+    import os
+    pytest.importorskip("torch")
+    path = os.path.join(os.path.dirname(restriction.__file__), "data", f"restriction_{net}.npz")
+    r = restriction.Restriction.load(path, "cpu")
+    assert r.net == net and r.features == "symbol" and 0.01 < r.tau < 1.0
